@@ -1,0 +1,175 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only builds initial states and parameter sets.  It holds none of
+the scheme's arithmetic, so that the GPU path and the CPU oracle can both be
+fed from it.  States are numpy arrays of shape (3, ny, nx) in the paper's
+dimensionless total variables q = (rho/rho0)(1, u1/c0, u2/c0) (eq. adim:q).
+
+Physical units are converted once here (eqs. renorm and phi-tdelta):
+    beta = 1 + B/(2A),   dt~ = delta / (c0 L),   A = p_amp / (rho0 c0^2),
+with L the wavelength c0/f for the plane-wave and focused-source cases.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+# Water (the plane-wave configuration names it; assumed for the others).
+RHO0 = 1000.0        # kg/m^3
+C0 = 1500.0          # m/s
+B_OVER_A = 5.0
+DIFFUSIVITY = 4.3e-6  # m^2/s, sound diffusivity delta
+
+
+def beta_of(b_over_a: float = B_OVER_A) -> float:
+    return 1.0 + 0.5 * b_over_a
+
+
+def delta_tilde(freq_hz: float, diffusivity: float = DIFFUSIVITY, c0: float = C0) -> float:
+    """dt~ = delta/(c0 L) with L = c0/f (one wavelength)."""
+    return diffusivity / (c0 * (c0 / freq_hz))
+
+
+def amplitude(p_pa: float, rho0: float = RHO0, c0: float = C0) -> float:
+    """Dimensionless density perturbation of a pressure amplitude, p = c0^2 rho."""
+    return p_pa / (rho0 * c0 * c0)
+
+
+def ambient(nx: int, ny: int) -> np.ndarray:
+    q = np.zeros((3, ny, nx), dtype=np.float64)
+    q[0] = 1.0
+    return q
+
+
+def cell_centres(nx: int, ny: int, dx: float, x0: float = 0.0, y0: float = 0.0):
+    x = x0 + (np.arange(nx) + 0.5) * dx
+    y = y0 + (np.arange(ny) + 0.5) * dx
+    return np.meshgrid(x, y)  # each (ny, nx)
+
+
+def plane_sine(nx: int, ny: int, amp: float, cells_per_wavelength: float) -> np.ndarray:
+    """Right-going sinusoid along x1: q1 = 1 + A sin(2 pi x), q2 = q1 - 1, q3 = 0
+    (the small-signal right-going relation of eq. OurTaylorS)."""
+    X, _ = cell_centres(nx, ny, 1.0 / cells_per_wavelength)
+    q = ambient(nx, ny)
+    q[0] = 1.0 + amp * np.sin(2.0 * np.pi * X)
+    q[1] = q[0] - 1.0
+    return q
+
+
+def gaussian_pulse(nx: int, ny: int, amp: float, sigma_cells: float, seed: int,
+                   max_offset_cells: int = 256) -> np.ndarray:
+    """Pressure Gaussian exp(-r^2/(2 sigma^2)) at rest, centre offset drawn from seed."""
+    rng = np.random.default_rng(seed)
+    off = min(max_offset_cells, max(0, min(nx, ny) // 2 - 4 * int(sigma_cells) - 1))
+    cx = nx / 2.0 + rng.integers(-off, off + 1)
+    cy = ny / 2.0 + rng.integers(-off, off + 1)
+    i = np.arange(nx) + 0.5
+    j = np.arange(ny) + 0.5
+    I, J = np.meshgrid(i, j)
+    r2 = (I - cx) ** 2 + (J - cy) ** 2
+    q = ambient(nx, ny)
+    q[0] = 1.0 + amp * np.exp(-r2 / (2.0 * sigma_cells ** 2))
+    return q
+
+
+def centred_gaussian(nx: int, ny: int, amp: float, sigma_cells: float) -> np.ndarray:
+    """Gaussian exactly at the domain centre (for mirror-symmetry checks)."""
+    i = np.arange(nx) + 0.5 - nx / 2.0
+    j = np.arange(ny) + 0.5 - ny / 2.0
+    I, J = np.meshgrid(i, j)
+    q = ambient(nx, ny)
+    q[0] = 1.0 + amp * np.exp(-(I * I + J * J) / (2.0 * sigma_cells ** 2))
+    return q
+
+
+def random_smooth(nx: int, ny: int, amp: float, seed: int, modes: int = 4) -> np.ndarray:
+    """Sum of a few random Fourier modes in all three fields (periodic-friendly)."""
+    rng = np.random.default_rng(seed)
+    X, Y = np.meshgrid(np.arange(nx) / nx, np.arange(ny) / ny)
+    q = ambient(nx, ny)
+    for k in range(3):
+        f = np.zeros((ny, nx))
+        for _ in range(modes):
+            kx, ky = rng.integers(0, 4, size=2)
+            ph = rng.uniform(0, 2 * np.pi)
+            f += rng.uniform(-1, 1) * np.cos(2 * np.pi * (kx * X + ky * Y) + ph)
+        q[k] += amp * f / modes
+    return q
+
+
+def random_cells(nx: int, ny: int, amp: float, seed: int) -> np.ndarray:
+    """Independent uniform perturbations per cell (rough data; exercises the limiter)."""
+    rng = np.random.default_rng(seed)
+    q = ambient(nx, ny)
+    q += amp * rng.uniform(-1.0, 1.0, size=q.shape)
+    return q
+
+
+def taylor_initial(nx: int, ny: int, dx: float, ratio: float, x0: float = 0.0,
+                   y0: float = 0.0, angle: float = 0.0, t: float = 0.0) -> np.ndarray:
+    """Taylor-shock profile of eq. OurTaylorS at time t (rotated by angle)."""
+    X, Y = cell_centres(nx, ny, dx, x0, y0)
+    c, s = np.cos(angle), np.sin(angle)
+    q = ambient(nx, ny)
+    q[0] = 1.0 - ratio * np.tanh(X * c + Y * s - t)
+    q[1] = (q[0] - 1.0) * c
+    q[2] = (q[0] - 1.0) * s
+    return q
+
+
+def tone_burst(nx: int, ny: int, amp: float, cells_per_wavelength: float, angle: float,
+               cycles: float = 4.0, centre=None) -> np.ndarray:
+    """Gaussian-enveloped plane tone burst travelling at `angle` (small-signal relation)."""
+    dx = 1.0 / cells_per_wavelength
+    X, Y = cell_centres(nx, ny, dx)
+    if centre is None:
+        centre = (nx * dx / 2.0, ny * dx / 2.0)
+    c, s = np.cos(angle), np.sin(angle)
+    xi = (X - centre[0]) * c + (Y - centre[1]) * s
+    w = amp * np.sin(2 * np.pi * xi) * np.exp(-(xi / (cycles / 2.0)) ** 2)
+    q = ambient(nx, ny)
+    q[0] = 1.0 + w
+    q[1] = w * c
+    q[2] = w * s
+    return q
+
+
+@dataclass
+class Workload:
+    """A named configuration: sizes, parameters and a state generator."""
+    name: str
+    nx: int
+    ny: int
+    steps: int
+    beta: float
+    delta: float
+    dx: float
+    nu_w: float
+    bc: tuple
+    q0: np.ndarray
+    geometry: int = 0
+    extra: dict = None
+
+
+BC_PERIODIC, BC_EXTRAP, BC_REFLECT, BC_TAYLOR, BC_HIFU = 0, 1, 2, 3, 4
+
+
+def plane_wave_512x8(steps: int = 2000) -> Workload:
+    """Plane-wave shock formation: 512x8 cells, periodic in y, extrapolation in
+    x, water, 1 MHz, 1 MPa, 40 cells per wavelength, MC limiter, CFL 0.9."""
+    eta = 40
+    q0 = plane_sine(512, 8, amplitude(1.0e6), eta)
+    return Workload("plane_wave_512x8", 512, 8, steps, beta_of(), delta_tilde(1.0e6),
+                    1.0 / eta, 0.9, (BC_EXTRAP, BC_EXTRAP, BC_PERIODIC, BC_PERIODIC), q0)
+
+
+def gaussian_2048(steps: int = 5000, n: int = 2048, seed: int = 2) -> Workload:
+    """2D Cartesian Gaussian pulse: n x n cells (2048^2 by default), peak 2 MPa,
+    sigma 8 cells, centre offset from the seed, extrapolation borders, 40 cells
+    per wavelength at 1 MHz (dx = 37.5 um)."""
+    eta = 40
+    q0 = gaussian_pulse(n, n, amplitude(2.0e6), 8.0, seed)
+    return Workload(f"gaussian_{n}x{n}", n, n, steps, beta_of(), delta_tilde(1.0e6),
+                    1.0 / eta, 0.9, (BC_EXTRAP,) * 4, q0)
