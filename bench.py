@@ -1,0 +1,362 @@
+"""Throughput of the finite-volume step on the 2048x2048 Gaussian-pulse workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+                    [--impl reference]
+
+One bench step = one full time step of the method (x1 sweep, x2 sweep +
+dissipative source, CFL dt update) over the 2048x2048 domain: peak 2 MPa,
+sigma 8 cells, centre offset from seed 2, extrapolation borders, water at
+1 MHz with 40 cells per wavelength, MC limiter, CFL 0.9.  The metric is
+cell-updates/s (one cell advanced one full step).
+
+Timing: W untimed steps, then K steps, each launched through the C ABI
+(fvna_step_timed: the three kernels with CUDA events between them on the
+library's stream), with L2 flushed (a 512 MB write on the same stream)
+before every timed step, outside the events.  `value` sums the K device
+step times.  `e2e` times the public call sequence a user makes for the
+whole 5000-step run from pinned host memory: fvna_init (host->device copy of
+the binary64 state), fvna_run, fvna_fields (device->host copy), destroy.
+
+With N > 1 (torchrun), every rank runs its own replica of the workload on
+its own GPU (the domains are independent: no data-path collective); the
+time is the max over ranks and `value` counts the cells of all ranks.
+
+`--impl reference` times the CPU oracle (plain C, one thread) on the host
+instead, one time step of the same workload per bench step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1311_3004_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "cell-updates/s"
+N_SIDE = 2048
+RUN_STEPS = 5000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--n", type=int, default=N_SIDE,
+                    help="domain side (the headline is 2048; other sizes are for profiling)")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--flush-mb", type=int, default=512,
+                    help="L2 flush buffer written before every timed step (0: none)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(n=N_SIDE):
+    return wl.gaussian_2048(steps=RUN_STEPS, n=n, seed=2)
+
+
+# ---------------------------------------------------------------- reference
+
+def oracle_params(w, oracle):
+    return oracle.Params(nx=w.nx, ny=w.ny, bc=w.bc, beta=w.beta, delta=w.delta, dx=w.dx,
+                         nu_w=w.nu_w)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    w = workload()
+    o = oracle.Oracle(oracle_params(w, oracle), w.q0)
+    o.run(args.warmup)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.run(1)
+        times.append(time.perf_counter() - t0)
+    o.close()
+    total = sum(times)
+    cells = w.nx * w.ny
+    v = cells * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"gaussian_pulse_{w.nx}x{w.ny}", "cells": cells,
+                   "time_steps_per_bench_step": 1, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} time steps of the {w.nx}x{w.ny} workload after "
+                                   f"{args.warmup} warm-up steps, single thread"},
+        "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(seconds_cap=20.0):
+    """The oracle as it stands on a bounded sample: full 2048^2 grid, as many
+    single time steps as fit in ~seconds_cap (at least 2)."""
+    import oracle
+    w = workload()
+    o = oracle.Oracle(oracle_params(w, oracle), w.q0)
+    o.run(1)
+    n, t_used = 0, 0.0
+    while n < 2 or (t_used < seconds_cap and n < 40):
+        t0 = time.perf_counter()
+        o.run(1)
+        t_used += time.perf_counter() - t0
+        n += 1
+    o.close()
+    return {"value": w.nx * w.ny * n / t_used, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{n} time steps of the {w.nx}x{w.ny} workload on one host thread "
+                      f"({t_used:.1f} s)"}
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fvna_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "power_w_max": max(r[2] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------- native
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1311_3004_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".inc")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; otherwise None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(kernel_key)
+    if not e or e.get("source_digest") != source_digest():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def measure_precision(torch, fvna, w, precision, steps, warmup, flush, do_flush=True):
+    stream = torch.cuda.current_stream()
+    cfg = fvna.make_config(precision=precision, beta=w.beta, delta=w.delta, dx=w.dx,
+                           nu_w=w.nu_w, steps_per_graph=1)
+    s = fvna.Solver(cfg, [fvna.make_domain(w.nx, w.ny, bc=w.bc)], [w.q0],
+                    stream=stream.cuda_stream)
+    for _ in range(warmup):
+        if do_flush:
+            flush.fill_(1.0)
+        s.step_timed()
+    n0 = s.launch_count()
+    per = []
+    for _ in range(steps):
+        if do_flush:
+            flush.fill_(1.0)   # > L2, on the library's stream, outside the events
+        per.append(s.step_timed())
+    launches = s.launch_count() - n0
+    st = s.stats(0)
+    s.close()
+    per = np.array(per)
+    return per, launches, st
+
+
+def run_native(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1311_3004_gb300 import fvna
+
+    w = workload(args.n)
+    cells = w.nx * w.ny
+    prec = fvna.FP32_PERT if args.precision == "fp32" else fvna.FP64
+    flush = torch.empty(max(1, args.flush_mb) * 1024 * 1024 // 4, dtype=torch.float32,
+                        device="cuda")
+    dev_index = torch.cuda.current_device()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev_index) as clk:
+        per, launches, st = measure_precision(torch, fvna, w, prec, args.steps, args.warmup,
+                                              flush, args.flush_mb > 0)
+    torch.cuda.synchronize()
+    step_ms = per.sum(axis=1)
+    total_s = float(step_ms.sum()) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        total_s = float(t.item())
+    value = cells * args.steps * world / total_s
+
+    # roofline of the dominant kernel (x1 sweep or x2 sweep + source)
+    esz = 4 if prec == fvna.FP32_PERT else 8
+    kern = ["k_sweep_x", "k_sweep_y"]
+    tot = per[:, :2].sum(axis=0)
+    k = int(np.argmax(tot))
+    avg_ms = float(tot[k] / args.steps)
+    alg_bytes = 2 * 3 * esz * cells          # read and write the three fields once
+    pk, pk_kind = peaks()
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    tkey = f"{kern[k]}_{args.precision}_{w.nx}x{w.ny}"
+    roof = {"bound": "hbm", "kernel": kern[k], "achieved": achieved,
+            "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+            "peak_source": pk_kind, "traffic": ncu_traffic(tkey),
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "kernel_ms": {"k_sweep_x": float(per[:, 0].mean()), "k_sweep_y": float(per[:, 1].mean()),
+                          "k_advance": float(per[:, 2].mean())}}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == fvna.FP32_PERT else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"gaussian_pulse_{w.nx}x{w.ny}", "cells_per_gpu": cells,
+                   "precision": args.precision, "time_steps_per_bench_step": 1,
+                   "l2": (f"flushed before every timed step ({args.flush_mb} MB write)"
+                          if args.flush_mb > 0 else "not flushed"),
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "sim": {"t": st["t"], "steps": st["steps"], "nu_mean": st["nu_mean"]},
+    }
+
+    if not args.no_e2e:
+        line["e2e"] = e2e(torch, fvna, w, prec)
+    if prec == fvna.FP32_PERT and not args.no_fp64:
+        per64, _, _ = measure_precision(torch, fvna, w, fvna.FP64, max(3, args.steps // 10), 2,
+                                        flush, args.flush_mb > 0)
+        line["fp64"] = {"value": cells * len(per64) / (per64.sum() / 1e3),
+                        "ms_per_step": float(per64.sum(axis=1).mean()),
+                        "kernel_ms": [float(x) for x in per64.mean(axis=0)]}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def e2e(torch, fvna, w, prec, reps=2):
+    """Whole-run call sequence from pinned host memory, host wall clock."""
+    cells = w.nx * w.ny
+    q_host = torch.from_numpy(w.q0).pin_memory()
+    out = torch.empty((3, w.ny, w.nx), dtype=torch.float64).pin_memory()
+    cfg = fvna.make_config(precision=prec, beta=w.beta, delta=w.delta, dx=w.dx, nu_w=w.nu_w,
+                           steps_per_graph=64)
+    times = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = fvna.Solver(cfg, [fvna.make_domain(w.nx, w.ny, bc=w.bc)], [q_host.numpy()])
+        s.run(max_steps=RUN_STEPS)
+        s.q(0, out=out.numpy())
+        s.close()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    best = min(times)
+    return {"value": cells * RUN_STEPS / best, "unit": METRIC,
+            "h2d_bytes_per_step": int(w.q0.nbytes), "d2h_bytes_per_step": int(out.numel() * 8),
+            "time_steps_per_e2e_step": RUN_STEPS, "seconds": best}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,193 @@
+/*
+ * fvna.h -- C ABI of the GB300 finite-volume nonlinear acoustics library.
+ *
+ * The library advances the dimensionless balance laws of Velasco-Segura &
+ * Rendon (arXiv 1311.3004), section 3, eq. OurSysAdim:
+ *     q_t + f_1(q)_x1 + f_2(q)_x2 = psi(q),
+ *     q = (rho/rho0)(1, u1/c0, u2/c0)                              (eq. adim:q)
+ * with the fractional-step method of eqs. fs:cl1, fs:cl2, fs:source: an x1
+ * sweep, an x2 sweep (entries 2 and 3 switched, end of section 3.2) and the
+ * dissipative source, each sweep being the high-resolution update of eq.
+ * fv-hr with Roe-linearised waves (section 3.2), fluctuations (eqs. fluc:m,
+ * fluc:p) and the MC-limited correction flux (eq. limiter).  The time step
+ * follows the CFL rule at the start of section 4.
+ *
+ * Every step runs in hand-written CUDA kernels for sm_103a; nothing here falls
+ * back to the CPU.  All entry points return FVNA_OK (0) or a negative error
+ * code; no C++ exception crosses this boundary.  A context is used by one host
+ * thread at a time.
+ *
+ * Data layout across the boundary.  A state is three planes of nx*ny binary64
+ * values in the paper's total variables (q1, q2, q3), plane k at offset
+ * k*nx*ny, row-major with x1 fastest: element (k, j, i) at k*nx*ny + j*nx + i.
+ * The library keeps its own device copy (SoA planes, rows padded to 32
+ * elements); in FVNA_FP32_PERT precision that copy holds (q1 - 1, q2, q3) in
+ * binary32, and conversions happen on the device.
+ */
+#ifndef FVNA_H
+#define FVNA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FVNA_OK            0
+#define FVNA_ERR_ARG      -1  /* invalid argument (sizes, enums, NULL, ...) */
+#define FVNA_ERR_CUDA     -2  /* a CUDA runtime call failed */
+#define FVNA_ERR_OOM      -3  /* device allocation failed */
+#define FVNA_ERR_NONREAL  -4  /* a Roe radicand was negative (section 3.2, S bound) */
+#define FVNA_ERR_CFL      -5  /* a step ran with nu > nu_max (section 4) */
+#define FVNA_ERR_NAN      -6  /* a wave speed was NaN */
+
+/* ---- enumerations ------------------------------------------------------ */
+enum fvna_precision {
+  FVNA_FP64 = 0,       /* binary64 total variables; rounding-identical to the reference formulas */
+  FVNA_FP32_PERT = 1   /* binary32 perturbations (q1-1, q2, q3), binary64 dt and budgets */
+};
+enum fvna_geometry {
+  FVNA_CARTESIAN = 0,     /* the paper's 2D Cartesian system */
+  FVNA_AXISYMMETRIC = 1   /* x1 = z, x2 = r, with the cylindrical source terms */
+};
+enum fvna_limiter {
+  FVNA_LIM_MC = 0,     /* monotonized central, eq. limiter */
+  FVNA_LIM_NONE = 1,   /* no correction: Godunov (section 3.1) */
+  FVNA_LIM_LW = 2      /* phi = 1: Lax-Wendroff (section 3.1) */
+};
+enum fvna_bc {
+  FVNA_BC_PERIODIC = 0,  /* wrap around (needs n >= 3 cells in that direction) */
+  FVNA_BC_EXTRAP = 1,    /* zero-order extrapolation (section 4.2) */
+  FVNA_BC_REFLECT = 2,   /* mirror, normal momentum negated (section 4.2); n >= 3 */
+  FVNA_BC_TAYLOR = 3,    /* Taylor-shock values of eq. OurTaylorS (section 4.1) */
+  FVNA_BC_HIFU = 4       /* focused drive of eq. hifuBC on the x1-low border */
+};
+enum fvna_field {
+  FVNA_FIELD_Q = 0,         /* 3*nx*ny binary64 total variables */
+  FVNA_FIELD_PRESSURE = 1,  /* nx*ny binary64 p'/(rho0 c0^2) = q1 - 1 (linear EOS, section 2) */
+  FVNA_FIELD_BUDGET = 2,    /* 3 binary64: sum over cells of (q1-1, q2, q3) after the last step */
+  FVNA_FIELD_STATS = 3      /* one fvna_stats */
+};
+
+/* ---- configuration ----------------------------------------------------- */
+typedef struct fvna_config {
+  int precision;        /* enum fvna_precision */
+  int geometry;         /* enum fvna_geometry */
+  int limiter;          /* enum fvna_limiter */
+  int sweeps;           /* bit 0: x1 sweep, bit 1: x2 sweep, bit 2: source; 7 = full step */
+  double beta;          /* nonlinearity 1 + B/2A (eq. OurSystem) */
+  double delta;         /* dimensionless diffusivity dt~ = delta/(c0 L) (eq. phi-tdelta) */
+  double dx;            /* cell size dx1 = dx2 (section 4) */
+  double nu_w;          /* wished CFL number nu_W (section 4) */
+  double nu_max;        /* a step with nu > nu_max ends the run with FVNA_ERR_CFL */
+  double dt_fixed;      /* > 0: use this dt for every step instead of the CFL rule */
+  int steps_per_graph;  /* steps captured per CUDA graph replay; 0 = default (32) */
+  int tile_x;           /* x1-sweep tile width (cells per warp row); 0 = default */
+  int tile_y;           /* x2-sweep tile height (rows per warp); 0 = default */
+  int reserved;
+} fvna_config;
+
+/* One domain.  Coordinates are those of the lower-left corner of cell (0,0);
+ * cell (i,j) has its centre at (x0 + (i+1/2) dx, y0 + (j+1/2) dx). */
+typedef struct fvna_domain {
+  int nx, ny;           /* cells; >= 1 each */
+  int bc[4];            /* enum fvna_bc for x1-low, x1-high, x2-low, x2-high */
+  int envelope;         /* HIFU envelope: 0 one-sided turn-on, 1 packet */
+  int reserved;
+  double x0, y0;        /* lower-left corner */
+  double t0;            /* initial time */
+  double dt0;           /* > 0: dt of the first step (resuming a run); 0: from a speed pass */
+  double taylor_ratio;  /* dt~/beta of the Taylor-shock border */
+  double taylor_angle;  /* propagation angle theta_T of that border */
+  double amp;           /* HIFU drive amplitude A */
+  double focal;         /* HIFU focal length F */
+  double aperture;      /* HIFU half aperture a (drive where 0 <= x2 <= a) */
+} fvna_domain;
+
+typedef struct fvna_stats {
+  long long steps;      /* steps taken since init */
+  double t;             /* current time */
+  double dt;            /* dt the CFL rule gives for the next step */
+  double dt_last;       /* dt of the last step */
+  double smax;          /* max |s| of the last step */
+  double nu_min, nu_max, nu_mean, nu_std;  /* CFL numbers of the unclamped steps */
+  int status;           /* 0 or the first error code seen (FVNA_ERR_NONREAL, _CFL, _NAN) */
+  int reserved;
+} fvna_stats;
+
+typedef struct fvna_ctx fvna_ctx;
+
+/* fvna_init -- create a context holding n_domains independent domains that
+ * advance together (one launch per sub-step covers all of them).
+ *   cfg          configuration shared by all domains (borrowed, copied)
+ *   doms         n_domains domain descriptions (borrowed, copied)
+ *   q0           n_domains pointers, each to 3*nx*ny binary64 total variables
+ *                laid out as described above (borrowed, copied)
+ *   q0_on_device nonzero if the q0 pointers are device pointers
+ *   stream       cudaStream_t the library enqueues on (borrowed; NULL = legacy default)
+ *   out          receives the new context, or NULL on failure
+ * The first dt comes from a speed-only pass over q0 (section 4), unless
+ * cfg->dt_fixed > 0 or the domain's dt0 > 0 (a resumed run: pass the state,
+ * t and the dt reported by FVNA_FIELD_STATS to continue bit for bit).  Returns FVNA_ERR_ARG for bad sizes or enums, FVNA_ERR_OOM
+ * when device memory runs out, FVNA_ERR_CUDA on any other CUDA failure. */
+int fvna_init(const fvna_config *cfg, int n_domains, const fvna_domain *doms,
+              const double *const *q0, int q0_on_device, void *stream, fvna_ctx **out);
+
+/* fvna_step -- enqueue nsteps full steps (asynchronous on the context's
+ * stream; no time limit).  Errors found on the device are reported by the
+ * next fvna_sync / fvna_run / fvna_fields call. */
+int fvna_step(fvna_ctx *ctx, long long nsteps);
+
+/* fvna_run -- advance until t reaches t_end (the step that would pass t_end is
+ * shortened to end on it) or max_steps steps were taken, whichever comes
+ * first; t_end <= current t means no time limit.  Blocks until done.  Returns
+ * FVNA_OK or the first device status (FVNA_ERR_NONREAL, _CFL, _NAN); on such
+ * an error the state is the one the failing step produced.  stats may be NULL;
+ * with several domains it receives domain 0's statistics. */
+int fvna_run(fvna_ctx *ctx, double t_end, long long max_steps, fvna_stats *stats);
+
+/* fvna_sync -- wait for the context's stream; return the device status. */
+int fvna_sync(fvna_ctx *ctx);
+
+/* fvna_fields -- copy one quantity of one domain into a caller buffer of
+ * `bytes` bytes (host or device, per dst_on_device); see enum fvna_field for
+ * sizes.  Synchronises the stream.  FVNA_ERR_ARG if bytes is too small. */
+int fvna_fields(fvna_ctx *ctx, int domain, int what, void *dst, size_t bytes, int dst_on_device);
+
+/* fvna_step_timed -- take one step with its kernels launched one by one (not
+ * from the step graph), CUDA events recorded between them on the context's
+ * stream, and block until it is done.  ms receives the device time of each
+ * launch in milliseconds: ms[0] x1 sweep (a plain copy if that sweep is off), ms[1] x2
+ * sweep + source, ms[2] dt update.  The step is identical to one of
+ * fvna_step.  Returns FVNA_OK or the device status after the step. */
+int fvna_step_timed(fvna_ctx *ctx, float ms[3]);
+
+/* fvna_launch_count -- kernels this context has enqueued so far (each kernel
+ * node of a graph replay counts once). */
+long long fvna_launch_count(const fvna_ctx *ctx);
+
+/* fvna_destroy -- free the context and its device memory (NULL is a no-op). */
+void fvna_destroy(fvna_ctx *ctx);
+
+/* fvna_strerror -- static text for a status code. */
+const char *fvna_strerror(int code);
+
+/* fvna_riemann -- run the device Roe solver of one x1-sweep interface on n
+ * host pairs (section 3.2; fluctuations of eqs. fluc:m, fluc:p), for checks.
+ *   qL, qR   n*3 binary64 total variables (q1, q2, q3) of cells i-1 and i
+ *   s        n*3 speeds s^1..s^3 (eqs. lambda1-lambda3)
+ *   W        n*9 waves, W[9*k + 3*p + c] = component c of W^p
+ *   amdq     n*3 left-going fluctuation A-dQ
+ *   apdq     n*3 right-going fluctuation A+dQ
+ * precision selects the binary64 or binary32-perturbation solver.  All
+ * buffers are host memory.  Returns FVNA_OK, or FVNA_ERR_NONREAL if some
+ * radicand was negative (outputs are still written). */
+int fvna_riemann(int precision, double beta, int n, const double *qL, const double *qR,
+                 double *s, double *W, double *amdq, double *apdq);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FVNA_H */

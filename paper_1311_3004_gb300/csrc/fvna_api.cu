@@ -1,0 +1,539 @@
+// fvna_api.cu -- host runtime behind include/fvna.h.
+//
+// A context owns, per domain, two sets of three SoA planes (the state and the
+// planes after the x1 sweep), rows padded to 32 elements; one array of
+// domain descriptors and one of per-domain device scalars (time, dt, CFL
+// statistics, status, budgets); and the two warp-tile lists of the sweeps.
+// A step is three launches on the caller's stream: the x1 sweep, the fused
+// x2 sweep + source, and the per-domain dt update.  Steps are captured once
+// into a CUDA graph of `steps_per_graph` steps and replayed; the kernels of a
+// finished domain return at once, so a replay may overrun the end of a run.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/fvna.h"
+#include "fvna_launch.h"
+
+using namespace fvna;
+
+struct fvna_ctx {
+  fvna_config cfg;
+  int ndom = 0;
+  std::vector<fvna_domain> doms;
+  std::vector<DomDev> dd;
+  DomDev *d_dd = nullptr;
+  DomScal *d_scal = nullptr;
+  Tile *d_tx = nullptr, *d_ty = nullptr;
+  int ntx = 0, nty = 0;
+  void *d_state = nullptr;
+  double *d_stage = nullptr;  // staging for host<->device state copies
+  size_t stage_bytes = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int gsteps = 32;
+  int tile_x = 32, tile_y = 64;
+  int blocks_x = 1, blocks_y = 1;
+  StepArgs args;    // common arguments (no tile list)
+  StepArgs args_x;  // x1 sweep: warp tiles of 32 rows x tile_x cells
+  StepArgs args_y;  // x2 sweep: warp tiles of 30 columns x tile_y rows
+  DomScal *h_scal = nullptr;  // pinned mirror
+  long long launches = 0;
+  int kernels_per_step = 3;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return FVNA_OK;
+  if (e == cudaErrorMemoryAllocation) return FVNA_ERR_OOM;
+  return FVNA_ERR_CUDA;
+}
+
+#define CK(call)                                \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_err(e_); \
+  } while (0)
+
+int status_code(int bits) {
+  if (bits & ST_NONREAL) return FVNA_ERR_NONREAL;
+  if (bits & ST_NAN) return FVNA_ERR_NAN;
+  if (bits & ST_CFL) return FVNA_ERR_CFL;
+  return FVNA_OK;
+}
+
+bool valid_bc(int b) { return b >= BC_PERIODIC && b <= BC_HIFU; }
+
+int validate(const fvna_config *c, int n, const fvna_domain *d, const double *const *q0) {
+  if (!c || n < 1 || !d || !q0) return FVNA_ERR_ARG;
+  if (c->precision != FVNA_FP64 && c->precision != FVNA_FP32_PERT) return FVNA_ERR_ARG;
+  if (c->geometry != FVNA_CARTESIAN && c->geometry != FVNA_AXISYMMETRIC) return FVNA_ERR_ARG;
+  if (c->limiter < FVNA_LIM_MC || c->limiter > FVNA_LIM_LW) return FVNA_ERR_ARG;
+  if (c->sweeps < 0 || c->sweeps > 7) return FVNA_ERR_ARG;
+  if (!(c->dx > 0.0) || !std::isfinite(c->dx)) return FVNA_ERR_ARG;
+  if (!std::isfinite(c->beta) || !(c->delta >= 0.0) || !std::isfinite(c->delta)) return FVNA_ERR_ARG;
+  if (!(c->dt_fixed > 0.0) && !(c->nu_w > 0.0)) return FVNA_ERR_ARG;
+  if (!(c->nu_max > 0.0)) return FVNA_ERR_ARG;
+  if (c->steps_per_graph < 0 || c->steps_per_graph > 4096) return FVNA_ERR_ARG;
+  if (c->tile_x != 0 && c->tile_x != 32 && c->tile_x != 64) return FVNA_ERR_ARG;
+  if (c->tile_y != 0 && (c->tile_y < 8 || c->tile_y > 4096)) return FVNA_ERR_ARG;
+  for (int k = 0; k < n; k++) {
+    const fvna_domain &D = d[k];
+    if (D.nx < 1 || D.ny < 1 || D.nx > (1 << 20) || D.ny > (1 << 20)) return FVNA_ERR_ARG;
+    if ((long long)D.nx * D.ny > (1ll << 33)) return FVNA_ERR_ARG;
+    if (!q0[k]) return FVNA_ERR_ARG;
+    for (int s = 0; s < 4; s++) {
+      if (!valid_bc(D.bc[s])) return FVNA_ERR_ARG;
+      int len = s < 2 ? D.nx : D.ny;
+      if ((D.bc[s] == BC_PERIODIC || D.bc[s] == BC_REFLECT) && len < 3) return FVNA_ERR_ARG;
+    }
+    // periodic borders come in pairs
+    if ((D.bc[0] == BC_PERIODIC) != (D.bc[1] == BC_PERIODIC)) return FVNA_ERR_ARG;
+    if ((D.bc[2] == BC_PERIODIC) != (D.bc[3] == BC_PERIODIC)) return FVNA_ERR_ARG;
+    if (D.bc[0] == BC_HIFU && !(D.focal > 0.0)) return FVNA_ERR_ARG;
+    if (!(D.dt0 >= 0.0) || !std::isfinite(D.t0)) return FVNA_ERR_ARG;
+  }
+  return FVNA_OK;
+}
+
+void free_ctx(fvna_ctx *c) {
+  if (!c) return;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  cudaFree(c->d_dd);
+  cudaFree(c->d_scal);
+  cudaFree(c->d_tx);
+  cudaFree(c->d_ty);
+  cudaFree(c->d_state);
+  cudaFree(c->d_stage);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  delete c;
+}
+
+int enqueue_steps_raw(fvna_ctx *c, cudaStream_t s, int nsteps) {
+  for (int i = 0; i < nsteps; i++) {
+    CK(launch_sweep_x(c->cfg.precision, c->tile_x, c->args_x, c->blocks_x, s));
+    CK(launch_sweep_y(c->cfg.precision, c->args_y, c->blocks_y, s));
+    CK(launch_advance(c->args, s));
+  }
+  return FVNA_OK;
+}
+
+int ensure_graph(fvna_ctx *c) {
+  if (c->gexec) return FVNA_OK;
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_steps_raw(c, c->cap, c->gsteps);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  if (rc != FVNA_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  CK(e);
+  c->graph = g;
+  CK(cudaGraphInstantiate(&c->gexec, g, 0));
+  return FVNA_OK;
+}
+
+int launch_graphs(fvna_ctx *c, long long n) {
+  for (long long i = 0; i < n; i++) {
+    CK(cudaGraphLaunch(c->gexec, c->stream));
+    c->launches += (long long)c->gsteps * c->kernels_per_step;
+  }
+  return FVNA_OK;
+}
+
+int read_scal(fvna_ctx *c) {
+  CK(cudaMemcpyAsync(c->h_scal, c->d_scal, sizeof(DomScal) * c->ndom, cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return FVNA_OK;
+}
+
+int first_status(const fvna_ctx *c) {
+  for (int d = 0; d < c->ndom; d++) {
+    int s = status_code(c->h_scal[d].status);
+    if (s != FVNA_OK) return s;
+  }
+  return FVNA_OK;
+}
+
+void fill_stats(const DomScal &S, fvna_stats *st) {
+  st->steps = S.step;
+  st->t = S.t;
+  st->dt = S.dt_cfl;
+  st->dt_last = S.dt_last;
+  st->smax = S.smax_last;
+  double n = S.nu_count > 0 ? (double)S.nu_count : 1.0;
+  st->nu_min = S.nu_count > 0 ? S.nu_min : 0.0;
+  st->nu_max = S.nu_count > 0 ? S.nu_max : 0.0;
+  st->nu_mean = S.nu_mean;
+  double var = S.nu_m2 / n;
+  st->nu_std = var > 0.0 ? std::sqrt(var) : 0.0;
+  st->status = status_code(S.status);
+  st->reserved = 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launch dispatch by precision
+// ---------------------------------------------------------------------------
+namespace fvna {
+cudaError_t prepare_kernels(int p, int tx) {
+  return p == FVNA_FP64 ? prepare_kernels_fp64(tx) : prepare_kernels_fp32(tx);
+}
+int occupancy_x(int p, int tx) { return p == FVNA_FP64 ? occupancy_x_fp64(tx) : occupancy_x_fp32(tx); }
+int occupancy_y(int p) { return p == FVNA_FP64 ? occupancy_y_fp64() : occupancy_y_fp32(); }
+cudaError_t launch_sweep_x(int p, int tx, const StepArgs &a, int b, cudaStream_t s) {
+  return p == FVNA_FP64 ? launch_sweep_x_fp64(tx, a, b, s) : launch_sweep_x_fp32(tx, a, b, s);
+}
+cudaError_t launch_sweep_y(int p, const StepArgs &a, int b, cudaStream_t s) {
+  return p == FVNA_FP64 ? launch_sweep_y_fp64(a, b, s) : launch_sweep_y_fp32(a, b, s);
+}
+cudaError_t launch_speeds(int p, const StepArgs &a, int dom, cudaStream_t s) {
+  return p == FVNA_FP64 ? launch_speeds_fp64(a, dom, s) : launch_speeds_fp32(a, dom, s);
+}
+cudaError_t launch_import(int p, const DomDev &d, const double *q0, cudaStream_t s) {
+  return p == FVNA_FP64 ? launch_import_fp64(d, q0, s) : launch_import_fp32(d, q0, s);
+}
+cudaError_t launch_export(int p, const DomDev &d, double *out, int what, cudaStream_t s) {
+  return p == FVNA_FP64 ? launch_export_fp64(d, out, what, s) : launch_export_fp32(d, out, what, s);
+}
+cudaError_t launch_riemann(int p, double beta, int n, const double *qL, const double *qR, double *s,
+                           double *W, double *am, double *ap, int *nr, cudaStream_t st) {
+  return p == FVNA_FP64 ? launch_riemann_fp64(beta, n, qL, qR, s, W, am, ap, nr, st)
+                        : launch_riemann_fp32(beta, n, qL, qR, s, W, am, ap, nr, st);
+}
+}  // namespace fvna
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *fvna_strerror(int code) {
+  switch (code) {
+    case FVNA_OK: return "ok";
+    case FVNA_ERR_ARG: return "invalid argument";
+    case FVNA_ERR_CUDA: return "CUDA runtime error";
+    case FVNA_ERR_OOM: return "device out of memory";
+    case FVNA_ERR_NONREAL: return "non-real wave speeds (state outside the hyperbolic region)";
+    case FVNA_ERR_CFL: return "CFL number above nu_max";
+    case FVNA_ERR_NAN: return "NaN wave speed";
+    default: return "unknown status";
+  }
+}
+
+static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
+                     const double *const *q0, int q0_on_device, void *stream, fvna_ctx *c) {
+  c->cfg = *cfg;
+  c->ndom = n;
+  c->doms.assign(doms, doms + n);
+  c->stream = (cudaStream_t)stream;
+  const int prec = cfg->precision;
+  const size_t esz = prec == FVNA_FP64 ? sizeof(double) : sizeof(float);
+  c->gsteps = cfg->steps_per_graph > 0 ? cfg->steps_per_graph : 32;
+  c->tile_x = cfg->tile_x ? cfg->tile_x : 32;
+  c->tile_y = cfg->tile_y ? cfg->tile_y : 64;
+  c->kernels_per_step = 3;
+
+  // state planes: 2 sets x 3 planes per domain, each plane 256-byte aligned
+  std::vector<size_t> offs(n);
+  size_t total = 0, max_cells = 0;
+  for (int d = 0; d < n; d++) {
+    size_t pitch = ((size_t)doms[d].nx + 31) / 32 * 32;
+    size_t plane = (pitch * doms[d].ny * esz + 255) / 256 * 256;
+    offs[d] = total;
+    total += 6 * plane;
+    max_cells = std::max(max_cells, (size_t)doms[d].nx * doms[d].ny);
+  }
+  CK(cudaMalloc(&c->d_state, total));
+  c->dd.resize(n);
+  for (int d = 0; d < n; d++) {
+    const fvna_domain &D = doms[d];
+    DomDev &g = c->dd[d];
+    std::memset(&g, 0, sizeof g);
+    g.nx = D.nx; g.ny = D.ny;
+    g.pitch = (D.nx + 31) / 32 * 32;
+    g.env = D.envelope;
+    for (int s = 0; s < 4; s++) g.bc[s] = D.bc[s];
+    g.x0 = D.x0; g.y0 = D.y0;
+    g.taylor_ratio = D.taylor_ratio;
+    g.taylor_ct = std::cos(D.taylor_angle);
+    g.taylor_st = std::sin(D.taylor_angle);
+    g.amp = D.amp; g.focal = D.focal; g.aperture = D.aperture;
+    g.dt0 = D.dt0;
+    size_t plane = ((size_t)g.pitch * D.ny * esz + 255) / 256 * 256;
+    char *base = (char *)c->d_state + offs[d];
+    for (int k = 0; k < 3; k++) {
+      g.qa[k] = base + k * plane;
+      g.qb[k] = base + (3 + k) * plane;
+    }
+  }
+  CK(cudaMemsetAsync(c->d_state, 0, total, c->stream));
+  CK(cudaMalloc(&c->d_dd, sizeof(DomDev) * n));
+  CK(cudaMemcpyAsync(c->d_dd, c->dd.data(), sizeof(DomDev) * n, cudaMemcpyHostToDevice, c->stream));
+  std::vector<DomScal> sc(n);
+  for (int d = 0; d < n; d++) {
+    std::memset(&sc[d], 0, sizeof(DomScal));
+    sc[d].t = doms[d].t0;
+    sc[d].nu_min = 1e300;
+    sc[d].done = 1;
+  }
+  CK(cudaMalloc(&c->d_scal, sizeof(DomScal) * n));
+  CK(cudaMemcpyAsync(c->d_scal, sc.data(), sizeof(DomScal) * n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMallocHost(&c->h_scal, sizeof(DomScal) * n));
+
+  // warp tiles
+  std::vector<Tile> tx, ty;
+  for (int d = 0; d < n; d++) {
+    for (int y = 0; y < doms[d].ny; y += XROWS)
+      for (int x = 0; x < doms[d].nx; x += c->tile_x) tx.push_back(Tile{d, x, y, 0});
+    for (int y = 0; y < doms[d].ny; y += c->tile_y)
+      for (int x = 0; x < doms[d].nx; x += YCOLS) ty.push_back(Tile{d, x, y, 0});
+  }
+  c->ntx = (int)tx.size();
+  c->nty = (int)ty.size();
+  CK(cudaMalloc(&c->d_tx, sizeof(Tile) * tx.size()));
+  CK(cudaMalloc(&c->d_ty, sizeof(Tile) * ty.size()));
+  CK(cudaMemcpyAsync(c->d_tx, tx.data(), sizeof(Tile) * tx.size(), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->d_ty, ty.data(), sizeof(Tile) * ty.size(), cudaMemcpyHostToDevice, c->stream));
+
+  // kernel set-up and persistent grid sizes
+  CK(prepare_kernels(prec, c->tile_x));
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int occx = std::max(1, occupancy_x(prec, c->tile_x));
+  int occy = std::max(1, occupancy_y(prec));
+  c->blocks_x = std::max(1, std::min((c->ntx + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, occx * sms));
+  c->blocks_y = std::max(1, std::min((c->nty + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, occy * sms));
+
+  StepArgs &a = c->args;
+  std::memset(&a, 0, sizeof a);
+  a.doms = c->d_dd;
+  a.scal = c->d_scal;
+  a.ndom = n;
+  a.beta = cfg->beta; a.delta = cfg->delta; a.dx = cfg->dx;
+  a.nu_w = cfg->nu_w; a.nu_max = cfg->nu_max; a.dt_fixed = cfg->dt_fixed;
+  a.limiter = cfg->limiter; a.geometry = cfg->geometry; a.sweeps = cfg->sweeps;
+  a.tile_y = c->tile_y;
+  c->args_x = a;
+  c->args_x.tiles = c->d_tx;
+  c->args_x.ntiles = c->ntx;
+  c->args_y = a;
+  c->args_y.tiles = c->d_ty;
+  c->args_y.ntiles = c->nty;
+
+  // initial state
+  if (!q0_on_device) {
+    c->stage_bytes = max_cells * 3 * sizeof(double);
+    CK(cudaMalloc(&c->d_stage, c->stage_bytes));
+  }
+  for (int d = 0; d < n; d++) {
+    const double *src = q0[d];
+    size_t bytes = (size_t)doms[d].nx * doms[d].ny * 3 * sizeof(double);
+    if (!q0_on_device) {
+      CK(cudaMemcpyAsync(c->d_stage, q0[d], bytes, cudaMemcpyHostToDevice, c->stream));
+      src = c->d_stage;
+    }
+    CK(launch_import(prec, c->dd[d], src, c->stream));
+    // speeds of the initial state -> first dt
+    StepArgs sa = a;
+    CK(launch_speeds(prec, sa, d, c->stream));
+  }
+  CK(launch_first_dt(a, c->stream));
+  CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  CK(cudaStreamSynchronize(c->stream));
+  return FVNA_OK;
+}
+
+int fvna_init(const fvna_config *cfg, int n_domains, const fvna_domain *doms,
+              const double *const *q0, int q0_on_device, void *stream, fvna_ctx **out) {
+  if (!out) return FVNA_ERR_ARG;
+  *out = nullptr;
+  int v = validate(cfg, n_domains, doms, q0);
+  if (v != FVNA_OK) return v;
+  fvna_ctx *c = new (std::nothrow) fvna_ctx();
+  if (!c) return FVNA_ERR_OOM;
+  int rc = init_impl(cfg, n_domains, doms, q0, q0_on_device, stream, c);
+  if (rc != FVNA_OK) {
+    cudaGetLastError();
+    free_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return FVNA_OK;
+}
+
+int fvna_step(fvna_ctx *c, long long nsteps) {
+  if (!c || nsteps < 0) return FVNA_ERR_ARG;
+  if (nsteps == 0) return FVNA_OK;
+  int rc = ensure_graph(c);
+  if (rc != FVNA_OK) return rc;
+  CK(launch_prepare(c->args, -1e300, nsteps, c->stream));
+  c->launches += 1;
+  return launch_graphs(c, (nsteps + c->gsteps - 1) / c->gsteps);
+}
+
+int fvna_run(fvna_ctx *c, double t_end, long long max_steps, fvna_stats *stats) {
+  if (!c || max_steps < 0) return FVNA_ERR_ARG;
+  int rc = ensure_graph(c);
+  if (rc != FVNA_OK) return rc;
+  CK(launch_prepare(c->args, t_end, max_steps, c->stream));
+  c->launches += 1;
+  long long left = max_steps > 0 ? (max_steps + c->gsteps - 1) / c->gsteps : 0;
+  long long batch = 1;
+  while (left > 0) {
+    long long nb = std::min(batch, left);
+    rc = launch_graphs(c, nb);
+    if (rc != FVNA_OK) return rc;
+    left -= nb;
+    rc = read_scal(c);
+    if (rc != FVNA_OK) return rc;
+    bool all_done = true;
+    for (int d = 0; d < c->ndom; d++) all_done &= c->h_scal[d].done != 0;
+    if (all_done) break;
+    batch = std::min<long long>(batch * 2, 64);
+  }
+  rc = read_scal(c);
+  if (rc != FVNA_OK) return rc;
+  if (stats) fill_stats(c->h_scal[0], stats);
+  return first_status(c);
+}
+
+int fvna_sync(fvna_ctx *c) {
+  if (!c) return FVNA_ERR_ARG;
+  int rc = read_scal(c);
+  if (rc != FVNA_OK) return rc;
+  return first_status(c);
+}
+
+int fvna_fields(fvna_ctx *c, int domain, int what, void *dst, size_t bytes, int dst_on_device) {
+  if (!c || !dst || domain < 0 || domain >= c->ndom) return FVNA_ERR_ARG;
+  const fvna_domain &D = c->doms[domain];
+  size_t cells = (size_t)D.nx * D.ny;
+  if (what == FVNA_FIELD_Q || what == FVNA_FIELD_PRESSURE) {
+    size_t need = cells * sizeof(double) * (what == FVNA_FIELD_Q ? 3 : 1);
+    if (bytes < need) return FVNA_ERR_ARG;
+    int w = what == FVNA_FIELD_Q ? 0 : 1;
+    if (dst_on_device) {
+      CK(launch_export(c->cfg.precision, c->dd[domain], (double *)dst, w, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    } else {
+      if (c->stage_bytes < need) {
+        cudaFree(c->d_stage);
+        c->d_stage = nullptr;
+        c->stage_bytes = 0;
+        size_t mx = 0;
+        for (const auto &d : c->doms) mx = std::max(mx, (size_t)d.nx * d.ny * 3 * sizeof(double));
+        CK(cudaMalloc(&c->d_stage, mx));
+        c->stage_bytes = mx;
+      }
+      CK(launch_export(c->cfg.precision, c->dd[domain], c->d_stage, w, c->stream));
+      CK(cudaMemcpyAsync(dst, c->d_stage, need, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
+    return FVNA_OK;
+  }
+  int rc = read_scal(c);
+  if (rc != FVNA_OK) return rc;
+  const DomScal &S = c->h_scal[domain];
+  if (what == FVNA_FIELD_BUDGET) {
+    if (bytes < 3 * sizeof(double)) return FVNA_ERR_ARG;
+    if (dst_on_device) CK(cudaMemcpy(dst, S.budget, 3 * sizeof(double), cudaMemcpyHostToDevice));
+    else std::memcpy(dst, S.budget, 3 * sizeof(double));
+    return FVNA_OK;
+  }
+  if (what == FVNA_FIELD_STATS) {
+    if (bytes < sizeof(fvna_stats)) return FVNA_ERR_ARG;
+    fvna_stats st;
+    fill_stats(S, &st);
+    if (dst_on_device) CK(cudaMemcpy(dst, &st, sizeof st, cudaMemcpyHostToDevice));
+    else std::memcpy(dst, &st, sizeof st);
+    return FVNA_OK;
+  }
+  return FVNA_ERR_ARG;
+}
+
+int fvna_step_timed(fvna_ctx *c, float ms[3]) {
+  if (!c || !ms) return FVNA_ERR_ARG;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (int i = 0; i < 4; i++) {
+    cudaError_t e = cudaEventCreate(&ev[i]);
+    if (e != cudaSuccess) {
+      for (int j = 0; j < i; j++) cudaEventDestroy(ev[j]);
+      return cuda_err(e);
+    }
+  }
+  cudaError_t e = launch_prepare(c->args, -1e300, 1, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->stream);
+  if (e == cudaSuccess)
+    e = launch_sweep_x(c->cfg.precision, c->tile_x, c->args_x, c->blocks_x, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
+  if (e == cudaSuccess) e = launch_sweep_y(c->cfg.precision, c->args_y, c->blocks_y, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->stream);
+  if (e == cudaSuccess) e = launch_advance(c->args, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[3], c->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[1], ev[1], ev[2]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[2], ev[2], ev[3]);
+  for (int i = 0; i < 4; i++) cudaEventDestroy(ev[i]);
+  if (e != cudaSuccess) return cuda_err(e);
+  c->launches += c->kernels_per_step + 1;
+  int rc = read_scal(c);
+  if (rc != FVNA_OK) return rc;
+  return first_status(c);
+}
+
+long long fvna_launch_count(const fvna_ctx *c) { return c ? c->launches : 0; }
+
+void fvna_destroy(fvna_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+int fvna_riemann(int precision, double beta, int n, const double *qL, const double *qR, double *s,
+                 double *W, double *amdq, double *apdq) {
+  if (precision != FVNA_FP64 && precision != FVNA_FP32_PERT) return FVNA_ERR_ARG;
+  if (n < 0 || (n > 0 && (!qL || !qR || !s || !W || !amdq || !apdq))) return FVNA_ERR_ARG;
+  if (n == 0) return FVNA_OK;
+  double *d = nullptr;
+  int *dnr = nullptr;
+  size_t per = 3 + 3 + 3 + 9 + 3 + 3;
+  CK(cudaMalloc(&d, sizeof(double) * per * n));
+  cudaError_t e = cudaMalloc(&dnr, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return cuda_err(e);
+  }
+  double *dqL = d, *dqR = d + 3 * n, *ds = d + 6 * n, *dW = d + 9 * n, *dam = d + 18 * n,
+         *dap = d + 21 * n;
+  int nr = 0;
+  e = cudaMemcpy(dqL, qL, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dqR, qR, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(dnr, 0, sizeof(int));
+  if (e == cudaSuccess) e = launch_riemann(precision, beta, n, dqL, dqR, ds, dW, dam, dap, dnr, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(s, ds, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(W, dW, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(amdq, dam, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(apdq, dap, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&nr, dnr, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  cudaFree(dnr);
+  if (e != cudaSuccess) return cuda_err(e);
+  return nr ? FVNA_ERR_NONREAL : FVNA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// fvna_fp64.cu -- binary64 kernels and the per-step bookkeeping.
+//
+// Compiled with -fmad=false: no product is fused into a sum, so every
+// expression rounds exactly as it is written (the order of the paper's
+// definitions, see fvna_device.cuh).  The dt/CFL bookkeeping lives here too,
+// because it is binary64 for both precisions (section 4: dt from the CFL
+// number of the previous step).
+#include "fvna_launch.h"
+#include "fvna_sweeps.cuh"
+
+#define POLICY P64
+#define SUFFIX fp64
+#include "fvna_precision.inc"
+
+namespace fvna {
+
+// End of a step for every domain: CFL number of the step just taken, the
+// CFL statistics (Welford), dt of the next step (nu_W dx / max|s|), time,
+// budgets, and whether the run goes on.  A step that would pass t_end is
+// shortened to end on it.
+__global__ void k_advance(StepArgs A) {
+  int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= A.ndom) return;
+  DomScal *S = A.scal + d;
+  if (S->done) return;
+  double smax = __longlong_as_double((long long)S->smax_bits);
+  int st = 0;
+  if (S->status_bits & ST_NONREAL) st |= ST_NONREAL;
+  if (smax != smax) st |= ST_NAN;
+  double dt = S->dt;
+  if (A.sweeps & 3) {
+    double nu = dt * smax / A.dx;
+    if (nu > A.nu_max) st |= ST_CFL;
+    if (!S->last) {
+      if (nu < S->nu_min) S->nu_min = nu;
+      if (nu > S->nu_max) S->nu_max = nu;
+      S->nu_count += 1;
+      double dd = nu - S->nu_mean;
+      S->nu_mean += dd / (double)S->nu_count;
+      S->nu_m2 += dd * (nu - S->nu_mean);
+    }
+  }
+  if (A.dt_fixed <= 0.0 && smax > 0.0) S->dt_cfl = A.nu_w * A.dx / smax;
+  S->dt_last = dt;
+  S->smax_last = smax;
+  S->t = S->last ? S->t_end : S->t + dt;
+  S->step += 1;
+  for (int k = 0; k < 3; k++) {
+    S->budget[k] = S->budget_acc[k];
+    S->budget_acc[k] = 0.0;
+  }
+  S->smax_bits = 0ull;
+  S->status_bits = 0;
+  S->status |= st;
+  if (S->steps_left > 0) S->steps_left -= 1;
+  if (S->status != 0 || S->steps_left == 0 || (S->timed && !(S->t < S->t_end))) {
+    S->done = 1;
+    return;
+  }
+  S->dt = S->dt_cfl;
+  S->last = 0;
+  if (S->timed && S->t + S->dt >= S->t_end) {
+    S->dt = S->t_end - S->t;
+    S->last = 1;
+  }
+}
+
+// Start of a run: time limit and step budget, dt of the first step.
+__global__ void k_prepare(StepArgs A, double t_end, long long max_steps) {
+  int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= A.ndom) return;
+  DomScal *S = A.scal + d;
+  S->smax_bits = 0ull;
+  S->status_bits = 0;
+  if (S->status != 0 || max_steps <= 0) {
+    S->done = 1;
+    return;
+  }
+  S->done = 0;
+  S->timed = t_end > S->t;
+  S->t_end = t_end;
+  S->steps_left = max_steps;
+  if (S->timed && !(S->t < S->t_end)) {
+    S->done = 1;
+    return;
+  }
+  S->dt = S->dt_cfl;
+  S->last = 0;
+  if (S->timed && S->t + S->dt >= S->t_end) {
+    S->dt = S->t_end - S->t;
+    S->last = 1;
+  }
+}
+
+// After the speed-only pass over the initial state: dt_0 = nu_W dx / max|s|.
+__global__ void k_first_dt(StepArgs A) {
+  int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= A.ndom) return;
+  DomScal *S = A.scal + d;
+  double s0 = __longlong_as_double((long long)S->smax_bits);
+  if (A.dt_fixed <= 0.0 && !(A.doms[d].dt0 > 0.0) && (S->status_bits & ST_NONREAL))
+    S->status |= ST_NONREAL;
+  const double dt0 = A.doms[d].dt0;
+  if (A.dt_fixed > 0.0) S->dt_cfl = A.dt_fixed;
+  else if (dt0 > 0.0) S->dt_cfl = dt0;
+  else S->dt_cfl = A.nu_w * A.dx / s0;
+  S->dt = S->dt_cfl;
+  S->smax_bits = 0ull;
+  S->status_bits = 0;
+  S->nu_min = 1e300;
+}
+
+cudaError_t launch_advance(const StepArgs &a, cudaStream_t s) {
+  k_advance<<<(a.ndom + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_prepare(const StepArgs &a, double t_end, long long max_steps, cudaStream_t s) {
+  k_prepare<<<(a.ndom + 127) / 128, 128, 0, s>>>(a, t_end, max_steps);
+  return cudaGetLastError();
+}
+cudaError_t launch_first_dt(const StepArgs &a, cudaStream_t s) {
+  k_first_dt<<<(a.ndom + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace fvna

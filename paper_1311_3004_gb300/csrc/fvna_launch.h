@@ -1,0 +1,57 @@
+// fvna_launch.h -- host-side launchers of the step kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fvna_types.h"
+
+namespace fvna {
+
+constexpr int WARPS_PER_BLOCK = 4;
+constexpr int YRING = 8;  // rows in flight per warp in the x2 sweep
+
+// shared memory of one block of each sweep (bytes)
+size_t smem_sweep_x(int precision, int tile_x);
+size_t smem_sweep_y(int precision);
+// one-time attribute setup (opt-in shared memory); returns cudaSuccess or the error
+cudaError_t prepare_kernels(int precision, int tile_x);
+// resident blocks per SM of each sweep
+int occupancy_x(int precision, int tile_x);
+int occupancy_y(int precision);
+
+cudaError_t launch_sweep_x(int precision, int tile_x, const StepArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_sweep_y(int precision, const StepArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_advance(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_prepare(const StepArgs &a, double t_end, long long max_steps, cudaStream_t s);
+cudaError_t launch_speeds(int precision, const StepArgs &a, int dom, cudaStream_t s);
+cudaError_t launch_first_dt(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_import(int precision, const DomDev &d, const double *q0, cudaStream_t s);
+cudaError_t launch_export(int precision, const DomDev &d, double *out, int what, cudaStream_t s);
+cudaError_t launch_riemann(int precision, double beta, int n, const double *qL, const double *qR,
+                           double *s, double *W, double *am, double *ap, int *nonreal,
+                           cudaStream_t st);
+
+// per-precision definitions (fvna_fp64.cu / fvna_fp32.cu)
+cudaError_t launch_sweep_x_fp64(int tile_x, const StepArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_sweep_y_fp64(const StepArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_speeds_fp64(const StepArgs &a, int dom, cudaStream_t s);
+cudaError_t launch_import_fp64(const DomDev &d, const double *q0, cudaStream_t s);
+cudaError_t launch_export_fp64(const DomDev &d, double *out, int what, cudaStream_t s);
+cudaError_t launch_riemann_fp64(double beta, int n, const double *qL, const double *qR, double *s,
+                                double *W, double *am, double *ap, int *nonreal, cudaStream_t st);
+cudaError_t prepare_kernels_fp64(int tile_x);
+int occupancy_x_fp64(int tile_x);
+int occupancy_y_fp64();
+
+cudaError_t launch_sweep_x_fp32(int tile_x, const StepArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_sweep_y_fp32(const StepArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_speeds_fp32(const StepArgs &a, int dom, cudaStream_t s);
+cudaError_t launch_import_fp32(const DomDev &d, const double *q0, cudaStream_t s);
+cudaError_t launch_export_fp32(const DomDev &d, double *out, int what, cudaStream_t s);
+cudaError_t launch_riemann_fp32(double beta, int n, const double *qL, const double *qR, double *s,
+                                double *W, double *am, double *ap, int *nonreal, cudaStream_t st);
+cudaError_t prepare_kernels_fp32(int tile_x);
+int occupancy_x_fp32(int tile_x);
+int occupancy_y_fp32();
+
+}  // namespace fvna

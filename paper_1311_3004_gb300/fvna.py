@@ -1,0 +1,265 @@
+"""Python binding of the C ABI in include/fvna.h (argument marshalling only).
+
+Every step of the method runs in the CUDA kernels of libfvna.so; this module
+converts arguments and raises FvnaError on a nonzero status.  If the library
+has not been built the import of `lib()` fails loudly: there is no CPU path.
+
+PyTorch serves only as the source of device memory and of the current CUDA
+stream when the caller passes torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfvna.so")
+
+FP64, FP32_PERT = 0, 1
+CARTESIAN, AXISYMMETRIC = 0, 1
+LIM_MC, LIM_NONE, LIM_LW = 0, 1, 2
+BC_PERIODIC, BC_EXTRAP, BC_REFLECT, BC_TAYLOR, BC_HIFU = 0, 1, 2, 3, 4
+FIELD_Q, FIELD_PRESSURE, FIELD_BUDGET, FIELD_STATS = 0, 1, 2, 3
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONREAL, ERR_CFL, ERR_NAN = 0, -1, -2, -3, -4, -5, -6
+
+
+class FvnaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("geometry", ctypes.c_int),
+                ("limiter", ctypes.c_int), ("sweeps", ctypes.c_int),
+                ("beta", ctypes.c_double), ("delta", ctypes.c_double), ("dx", ctypes.c_double),
+                ("nu_w", ctypes.c_double), ("nu_max", ctypes.c_double),
+                ("dt_fixed", ctypes.c_double), ("steps_per_graph", ctypes.c_int),
+                ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class Domain(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("bc", ctypes.c_int * 4),
+                ("envelope", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("t0", ctypes.c_double),
+                ("dt0", ctypes.c_double), ("taylor_ratio", ctypes.c_double), ("taylor_angle", ctypes.c_double),
+                ("amp", ctypes.c_double), ("focal", ctypes.c_double),
+                ("aperture", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("t", ctypes.c_double), ("dt", ctypes.c_double),
+                ("dt_last", ctypes.c_double), ("smax", ctypes.c_double),
+                ("nu_min", ctypes.c_double), ("nu_max", ctypes.c_double),
+                ("nu_mean", ctypes.c_double), ("nu_std", ctypes.c_double),
+                ("status", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "reserved"}
+
+
+SYMBOLS = ["fvna_init", "fvna_step", "fvna_run", "fvna_sync", "fvna_fields",
+           "fvna_step_timed", "fvna_launch_count", "fvna_destroy", "fvna_strerror", "fvna_riemann"]
+
+_lib = None
+
+
+def lib():
+    """Load libfvna.so (raises if it was not built: no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not built; run __graft_entry__.build() or "
+                          "python -m paper_1311_3004_gb300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    L.fvna_init.restype = ctypes.c_int
+    L.fvna_init.argtypes = [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(Domain),
+                            ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, vp,
+                            ctypes.POINTER(vp)]
+    L.fvna_step.restype = ctypes.c_int
+    L.fvna_step.argtypes = [vp, ctypes.c_longlong]
+    L.fvna_run.restype = ctypes.c_int
+    L.fvna_run.argtypes = [vp, ctypes.c_double, ctypes.c_longlong, ctypes.POINTER(Stats)]
+    L.fvna_sync.restype = ctypes.c_int
+    L.fvna_sync.argtypes = [vp]
+    L.fvna_fields.restype = ctypes.c_int
+    L.fvna_fields.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t, ctypes.c_int]
+    L.fvna_step_timed.restype = ctypes.c_int
+    L.fvna_step_timed.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    L.fvna_launch_count.restype = ctypes.c_longlong
+    L.fvna_launch_count.argtypes = [vp]
+    L.fvna_destroy.restype = None
+    L.fvna_destroy.argtypes = [vp]
+    L.fvna_strerror.restype = ctypes.c_char_p
+    L.fvna_strerror.argtypes = [ctypes.c_int]
+    L.fvna_riemann.restype = ctypes.c_int
+    L.fvna_riemann.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, dp, dp]
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().fvna_strerror(code).decode()
+    except ImportError:
+        return f"status {code}"
+
+
+def _check(rc: int, where: str) -> int:
+    if rc != OK:
+        raise FvnaError(rc, where)
+    return rc
+
+
+def make_config(precision=FP64, geometry=CARTESIAN, limiter=LIM_MC, sweeps=7, beta=3.5,
+                delta=0.0, dx=1.0, nu_w=0.9, nu_max=1.0, dt_fixed=0.0, steps_per_graph=0,
+                tile_x=0, tile_y=0) -> Config:
+    return Config(precision, geometry, limiter, sweeps, beta, delta, dx, nu_w, nu_max, dt_fixed,
+                  steps_per_graph, tile_x, tile_y, 0)
+
+
+def make_domain(nx, ny, bc=(BC_EXTRAP,) * 4, envelope=0, x0=0.0, y0=0.0, t0=0.0, dt0=0.0,
+                taylor_ratio=0.0, taylor_angle=0.0, amp=0.0, focal=1.0, aperture=0.0) -> Domain:
+    return Domain(nx, ny, (ctypes.c_int * 4)(*bc), envelope, 0, x0, y0, t0, dt0, taylor_ratio,
+                  taylor_angle, amp, focal, aperture)
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+class Solver:
+    """A context of one or more domains advancing together.
+
+    q0: one array per domain of shape (3, ny, nx), binary64 total variables;
+    numpy arrays (host) or torch CUDA tensors (device), not mixed.
+    """
+
+    def __init__(self, config: Config, domains: Sequence[Domain], q0: Sequence, stream=None):
+        L = lib()
+        self.config = config
+        self.domains = list(domains)
+        n = len(self.domains)
+        on_dev = False
+        keep = []
+        ptrs = (ctypes.c_void_p * n)()
+        for i, (d, q) in enumerate(zip(self.domains, q0)):
+            if hasattr(q, "is_cuda") and q.is_cuda:
+                import torch
+                q = q.to(torch.float64).contiguous()
+                assert tuple(q.shape) == (3, d.ny, d.nx)
+                on_dev = True
+                ptrs[i] = q.data_ptr()
+            else:
+                q = np.ascontiguousarray(q, dtype=np.float64)
+                assert q.shape == (3, d.ny, d.nx), (q.shape, d.ny, d.nx)
+                ptrs[i] = q.ctypes.data
+            keep.append(q)
+        if stream is None:
+            stream = _current_stream()
+        self.stream = stream
+        darr = (Domain * n)(*self.domains)
+        h = ctypes.c_void_p()
+        _check(L.fvna_init(ctypes.byref(config), n, darr, ptrs, int(on_dev),
+                           ctypes.c_void_p(stream), ctypes.byref(h)), "fvna_init")
+        self._h = h
+
+    # -- stepping -----------------------------------------------------------
+    def step(self, nsteps: int) -> None:
+        _check(lib().fvna_step(self._h, int(nsteps)), "fvna_step")
+
+    def run(self, t_end: float = -np.inf, max_steps: int = 2 ** 62, check: bool = True) -> dict:
+        st = Stats()
+        t_end = float(t_end) if np.isfinite(t_end) else -1e300
+        rc = lib().fvna_run(self._h, t_end, int(max_steps), ctypes.byref(st))
+        if check:
+            _check(rc, "fvna_run")
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
+
+    def step_timed(self):
+        """One step with per-kernel device times (ms): (x1 sweep, x2 sweep + source, dt update)."""
+        ms = (ctypes.c_float * 3)()
+        _check(lib().fvna_step_timed(self._h, ms), "fvna_step_timed")
+        return float(ms[0]), float(ms[1]), float(ms[2])
+
+    def sync(self) -> int:
+        return lib().fvna_sync(self._h)
+
+    # -- outputs ------------------------------------------------------------
+    def q(self, domain: int = 0, out=None):
+        """State of one domain as (3, ny, nx) binary64 (numpy, or into a torch CUDA tensor)."""
+        d = self.domains[domain]
+        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            _check(lib().fvna_fields(self._h, domain, FIELD_Q, ctypes.c_void_p(out.data_ptr()),
+                                     out.numel() * out.element_size(), 1), "fvna_fields")
+            return out
+        arr = np.empty((3, d.ny, d.nx), dtype=np.float64) if out is None else out
+        _check(lib().fvna_fields(self._h, domain, FIELD_Q, ctypes.c_void_p(arr.ctypes.data),
+                                 arr.nbytes, 0), "fvna_fields")
+        return arr
+
+    def pressure(self, domain: int = 0):
+        d = self.domains[domain]
+        arr = np.empty((d.ny, d.nx), dtype=np.float64)
+        _check(lib().fvna_fields(self._h, domain, FIELD_PRESSURE, ctypes.c_void_p(arr.ctypes.data),
+                                 arr.nbytes, 0), "fvna_fields")
+        return arr
+
+    def budget(self, domain: int = 0):
+        arr = np.zeros(3, dtype=np.float64)
+        _check(lib().fvna_fields(self._h, domain, FIELD_BUDGET, ctypes.c_void_p(arr.ctypes.data),
+                                 arr.nbytes, 0), "fvna_fields")
+        return arr
+
+    def stats(self, domain: int = 0) -> dict:
+        st = Stats()
+        _check(lib().fvna_fields(self._h, domain, FIELD_STATS, ctypes.cast(ctypes.byref(st),
+                                 ctypes.c_void_p), ctypes.sizeof(st), 0), "fvna_fields")
+        return st.as_dict()
+
+    def launch_count(self) -> int:
+        return int(lib().fvna_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fvna_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def riemann(precision: int, beta: float, qL, qR):
+    """Device Roe solver on n pairs of cells (n, 3): returns s (n,3), W (n,3,3),
+    amdq (n,3), apdq (n,3), nonreal flag."""
+    qL = np.ascontiguousarray(qL, dtype=np.float64).reshape(-1, 3)
+    qR = np.ascontiguousarray(qR, dtype=np.float64).reshape(-1, 3)
+    n = qL.shape[0]
+    s = np.zeros((n, 3))
+    W = np.zeros((n, 3, 3))
+    am = np.zeros((n, 3))
+    ap = np.zeros((n, 3))
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib().fvna_riemann(precision, beta, n, qL.ctypes.data_as(dp), qR.ctypes.data_as(dp),
+                            s.ctypes.data_as(dp), W.ctypes.data_as(dp), am.ctypes.data_as(dp),
+                            ap.ctypes.data_as(dp))
+    if rc not in (OK, ERR_NONREAL):
+        raise FvnaError(rc, "fvna_riemann")
+    return s, W, am, ap, rc == ERR_NONREAL

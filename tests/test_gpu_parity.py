@@ -1,0 +1,309 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle on
+the same seeded inputs.
+
+FP64 bar: perturbation-relative L_inf <= 1e-12 (the FP64 kernels evaluate
+the scheme's formulas in the oracle's order without FMA contraction, so the
+expected difference is zero away from driven borders, whose tanh/sin/exp come
+from different math libraries on the two sides).
+FP32 (perturbation variables) bar: peak-pressure and L2 errors <= 1e-5
+relative to the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+from paper_1311_3004_gb300 import fvna
+from paper_1311_3004_gb300 import workloads as wl
+
+from helpers import (Case, gpu_config, gpu_domain, pert_rel_linf, pressure_errors, run_gpu,
+                     run_oracle)
+
+pytestmark = pytest.mark.gpu
+
+P, E, R, T, H = (fvna.BC_PERIODIC, fvna.BC_EXTRAP, fvna.BC_REFLECT, fvna.BC_TAYLOR,
+                 fvna.BC_HIFU)
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1311_3004_gb300 import build
+    build.build()
+
+
+def test_riemann_fp64_bit_identical_to_oracle():
+    import oracle
+    rng = np.random.default_rng(11)
+    n = 500
+    qL = np.array([1.0, 0, 0]) + 2e-2 * rng.uniform(-1, 1, (n, 3))
+    qR = qL + 2e-2 * rng.uniform(-1, 1, (n, 3))
+    s, W, am, ap, nr = fvna.riemann(fvna.FP64, 3.7, qL, qR)
+    assert not nr
+    for k in range(n):
+        so, Wo, amo, apo, nro = oracle.interface(3.7, qL[k], qR[k])
+        np.testing.assert_array_equal(s[k], so)
+        np.testing.assert_array_equal(W[k], Wo)
+        np.testing.assert_array_equal(am[k], amo)
+        np.testing.assert_array_equal(ap[k], apo)
+
+
+def test_riemann_fp32_close_to_oracle():
+    import oracle
+    rng = np.random.default_rng(12)
+    n = 300
+    qL = np.array([1.0, 0, 0]) + 1e-3 * rng.uniform(-1, 1, (n, 3))
+    qR = qL + 1e-3 * rng.uniform(-1, 1, (n, 3))
+    s, W, am, ap, nr = fvna.riemann(fvna.FP32_PERT, 3.5, qL, qR)
+    for k in range(n):
+        so, Wo, amo, apo, _ = oracle.interface(3.5, qL[k], qR[k])
+        assert np.max(np.abs(s[k] - so)) < 3e-7
+        scale = np.max(np.abs(qR[k] - qL[k]))
+        assert np.max(np.abs(W[k] - Wo)) < 2e-6 * scale
+        assert np.max(np.abs(am[k] - amo)) < 2e-6 * scale
+
+
+def test_riemann_flags_nonreal():
+    # rho/rho0 = 0.6 with a velocity above sqrt(S): non-real speeds (section 3.2)
+    q = np.array([[0.6, 0.6 * 1.5, 0.0]])
+    *_, nr = fvna.riemann(fvna.FP64, 4.8, q, q)
+    assert nr
+
+
+def _cases():
+    cs = []
+    q = wl.random_smooth(67, 45, 2e-3, seed=21)
+    cs.append(("periodic_ragged", Case(67, 45, q, bc=(P, P, P, P), delta=3e-3), 40))
+    q = wl.random_cells(70, 37, 1e-3, seed=22)
+    cs.append(("extrap_rough", Case(70, 37, q, bc=(E, E, E, E), delta=1e-3), 25))
+    q = wl.random_smooth(41, 39, 2e-3, seed=23)
+    cs.append(("reflect_all", Case(41, 39, q, bc=(R, R, R, R), delta=2e-3), 30))
+    q = wl.random_cells(35, 66, 1e-3, seed=24)
+    cs.append(("mixed_borders", Case(35, 66, q, bc=(P, P, R, E), delta=1e-3, beta=4.8), 30))
+    q = wl.random_smooth(50, 50, 2e-3, seed=25)
+    for lim, name in [(fvna.LIM_NONE, "godunov"), (fvna.LIM_LW, "lax_wendroff")]:
+        cs.append((name, Case(50, 50, q, bc=(P, P, E, E), delta=1e-3, limiter=lim), 20))
+    q = wl.random_cells(33, 29, 1e-3, seed=26)
+    for sw in (1, 2, 3, 4, 5, 6):
+        cs.append((f"sweeps_{sw}", Case(33, 29, q, bc=(P, P, E, E), sweeps=sw,
+                                        delta=1e-2, dt_fixed=0.01), 12))
+    q = wl.random_cells(100, 1, 1e-3, seed=27)
+    cs.append(("one_row", Case(100, 1, q, bc=(P, P, E, E), delta=1e-3), 30))
+    q = wl.random_cells(1, 90, 1e-3, seed=28)
+    cs.append(("one_column", Case(1, 90, q, bc=(E, E, R, R), delta=1e-3), 30))
+    q = wl.centred_gaussian(64, 48, 5e-3, 4.0)
+    cs.append(("gaussian_fixed_dt", Case(64, 48, q, delta=2e-3, dt_fixed=0.02), 40))
+    return cs
+
+
+@pytest.mark.parametrize("name,case,steps", _cases(), ids=[c[0] for c in _cases()])
+def test_step_parity_fp64(name, case, steps):
+    qo, so = run_oracle(case, steps)
+    qg, sg = run_gpu(case, steps)
+    assert so["status"] == 0 and sg["rc"] == 0
+    assert sg["steps"] == so["step"] == steps
+    err = pert_rel_linf(qg, qo)
+    assert err <= TOL64, err
+    assert sg["t"] == so["t"]
+    assert sg["nu_mean"] == pytest.approx(so["nu_mean"], rel=1e-14, abs=1e-15)
+
+
+@pytest.mark.parametrize("tile_x,tile_y", [(32, 8), (64, 16), (32, 128), (64, 64)])
+def test_tile_shapes_give_identical_results(tile_x, tile_y):
+    q = wl.random_cells(150, 140, 1e-3, seed=31)
+    c = Case(150, 140, q, bc=(P, P, E, R), delta=2e-3)
+    qo, _ = run_oracle(c, 15)
+    qg, _ = run_gpu(c, 15, tile_x=tile_x, tile_y=tile_y)
+    assert pert_rel_linf(qg, qo) <= TOL64
+
+
+def test_time_limited_run_ends_on_t_end():
+    q = wl.random_smooth(48, 40, 1e-3, seed=32)
+    c = Case(48, 40, q, bc=(P, P, P, P), delta=1e-3)
+    qo, so = run_oracle(c, 10 ** 6, t_end=0.3)
+    qg, sg = run_gpu(c, 10 ** 6, t_end=0.3)
+    assert sg["t"] == so["t"] == 0.3
+    assert sg["steps"] == so["step"]
+    assert pert_rel_linf(qg, qo) <= TOL64
+    assert sg["nu_std"] == pytest.approx(so["nu_std"], rel=1e-6, abs=1e-15)
+
+
+def test_taylor_border_parity():
+    """Driven Taylor-shock borders (eq. OurTaylorS) rotated by theta_T = pi/8."""
+    ratio, beta = 1e-4, 3.5
+    n, dx = 60, 1.0 / 10
+    q = wl.taylor_initial(n, n, dx, ratio, x0=-3.0, y0=-3.0, angle=np.pi / 8)
+    c = Case(n, n, q, bc=(T, T, T, T), beta=beta, delta=ratio * beta, dx=dx, x0=-3.0, y0=-3.0,
+             taylor_ratio=ratio, taylor_angle=np.pi / 8)
+    qo, so = run_oracle(c, 40)
+    qg, sg = run_gpu(c, 40)
+    # the border values come from libm (oracle) and CUDA (kernels): a few ulp
+    # of the total state q1 ~ 1, i.e. ~1e-12 of the 1e-4 perturbation
+    assert pert_rel_linf(qg, qo) <= 5e-11
+    assert np.max(np.abs(qg - qo)) <= 1e-14
+
+
+def test_hifu_drive_parity():
+    """Focused drive of eq. hifuBC on the x1-low border, reflective axis below."""
+    n1, n2 = 90, 50
+    q = wl.ambient(n1, n2)
+    c = Case(n1, n2, q, bc=(H, E, R, E), beta=4.8, delta=2.974e-4, dx=1.0 / 10, amp=4.217e-4,
+             focal=5.0, aperture=3.0, envelope=1, t0=-4.0)
+    qo, so = run_oracle(c, 80)
+    qg, sg = run_gpu(c, 80)
+    assert np.max(np.abs(qo[0] - 1)) > 1e-5
+    assert pert_rel_linf(qg, qo) <= 5e-11
+    assert np.max(np.abs(qg - qo)) <= 1e-14
+
+
+def test_axisymmetric_parity():
+    n1, n2 = 64, 40
+    q = wl.centred_gaussian(n1, n2, 2e-3, 5.0)
+    c = Case(n1, n2, q, bc=(E, E, R, E), geometry=1, delta=2e-3, dx=1.0 / 16, y0=0.0)
+    qo, so = run_oracle(c, 30)
+    qg, sg = run_gpu(c, 30)
+    assert pert_rel_linf(qg, qo) <= TOL64
+
+
+def test_multi_domain_context_matches_separate_oracles():
+    cases = [
+        Case(70, 33, wl.random_cells(70, 33, 1e-3, seed=41), bc=(P, P, E, E), delta=1e-3,
+             dt_fixed=0.01),
+        Case(31, 90, wl.random_smooth(31, 90, 2e-3, seed=42), bc=(E, E, R, R), delta=1e-3,
+             dt_fixed=0.01),
+        Case(5, 5, wl.random_cells(5, 5, 1e-3, seed=43), bc=(E, E, E, E), delta=1e-3,
+             dt_fixed=0.01),
+    ]
+    s = fvna.Solver(gpu_config(cases[0]), [gpu_domain(c) for c in cases], [c.q0 for c in cases])
+    s.run(max_steps=20)
+    for k, c in enumerate(cases):
+        qo, so = run_oracle(c, 20)
+        assert pert_rel_linf(s.q(k), qo) <= TOL64, k
+    s.close()
+
+
+def test_multi_domain_own_cfl_dt():
+    """Each domain keeps its own CFL-controlled dt."""
+    cases = [Case(40, 40, wl.centred_gaussian(40, 40, a, 3.0), delta=1e-3) for a in (1e-3, 5e-2)]
+    s = fvna.Solver(gpu_config(cases[0]), [gpu_domain(c) for c in cases], [c.q0 for c in cases])
+    s.run(max_steps=25)
+    for k, c in enumerate(cases):
+        qo, so = run_oracle(c, 25)
+        assert pert_rel_linf(s.q(k), qo) <= TOL64
+        assert s.stats(k)["t"] == so["t"]
+    assert s.stats(0)["t"] != s.stats(1)["t"]
+    s.close()
+
+
+def test_resume_is_bit_identical():
+    q = wl.random_smooth(64, 64, 2e-3, seed=51)
+    c = Case(64, 64, q, bc=(P, P, E, E), delta=2e-3)
+    full, _ = run_gpu(c, 40)
+    s = fvna.Solver(gpu_config(c), [gpu_domain(c)], [q])
+    s.run(max_steps=20)
+    mid, st = s.q(0), s.stats(0)
+    s.close()
+    s2 = fvna.Solver(gpu_config(c), [gpu_domain(c, dt0=st["dt"], t0=st["t"])], [mid])
+    s2.run(max_steps=20)
+    np.testing.assert_array_equal(s2.q(0), full)
+    s2.close()
+
+
+def test_step_and_run_agree_and_count_launches():
+    q = wl.random_smooth(40, 40, 1e-3, seed=52)
+    c = Case(40, 40, q, bc=(P, P, P, P), delta=1e-3)
+    s = fvna.Solver(gpu_config(c, steps_per_graph=8), [gpu_domain(c)], [q])
+    s.step(13)
+    assert s.sync() == 0
+    assert s.stats(0)["steps"] == 13
+    n = s.launch_count()
+    assert n >= 13 * 3
+    qo, _ = run_oracle(c, 13)
+    assert pert_rel_linf(s.q(0), qo) <= TOL64
+    s.close()
+
+
+def test_device_pointer_input_and_output():
+    torch = pytest.importorskip("torch")
+    q = wl.random_cells(37, 23, 1e-3, seed=53)
+    c = Case(37, 23, q, bc=(E, E, P, P), delta=1e-3)
+    qd = torch.from_numpy(q).cuda()
+    s = fvna.Solver(gpu_config(c), [gpu_domain(c)], [qd])
+    s.run(max_steps=10)
+    out = torch.empty((3, 23, 37), dtype=torch.float64, device="cuda")
+    s.q(0, out=out)
+    qo, _ = run_oracle(c, 10)
+    assert pert_rel_linf(out.cpu().numpy(), qo) <= TOL64
+    s.close()
+
+
+def test_budget_sums_the_state():
+    q = wl.random_smooth(50, 44, 2e-3, seed=54)
+    c = Case(50, 44, q, bc=(P, P, P, P), delta=2e-3)
+    s = fvna.Solver(gpu_config(c), [gpu_domain(c)], [q])
+    s.run(max_steps=30)
+    b = s.budget(0)
+    qq = s.q(0)
+    want = np.array([np.sum(qq[0] - 1.0), np.sum(qq[1]), np.sum(qq[2])])
+    assert np.max(np.abs(b - want)) < 1e-12
+    # periodic: the sums are conserved (section 3: flux differences telescope)
+    want0 = np.array([np.sum(q[0] - 1.0), np.sum(q[1]), np.sum(q[2])])
+    assert np.max(np.abs(b - want0)) < 1e-12
+    s.close()
+
+
+# ------------------------------------------------------------------ errors
+
+def test_nonreal_state_is_reported():
+    q = wl.centred_gaussian(32, 32, -0.45, 3.0)   # rho/rho0 down to 0.55
+    q[1] = 0.5
+    c = Case(32, 32, q, beta=4.8)
+    s = fvna.Solver(gpu_config(c), [gpu_domain(c)], [q])
+    st = s.run(max_steps=5, check=False)
+    assert st["rc"] in (fvna.ERR_NONREAL, fvna.ERR_NAN)
+    s.close()
+
+
+def test_cfl_violation_is_reported():
+    q = wl.random_smooth(32, 32, 1e-3, seed=55)
+    c = Case(32, 32, q, bc=(P, P, P, P), dt_fixed=2.0 / 32)  # nu ~ 2
+    s = fvna.Solver(gpu_config(c), [gpu_domain(c)], [q])
+    st = s.run(max_steps=5, check=False)
+    assert st["rc"] == fvna.ERR_CFL
+    assert st["steps"] == 1   # stops after the offending step
+    s.close()
+
+
+def test_nan_input_is_reported():
+    q = wl.random_smooth(32, 32, 1e-3, seed=56)
+    q[1, 5, 7] = np.nan
+    c = Case(32, 32, q, bc=(P, P, P, P), dt_fixed=0.01)
+    s = fvna.Solver(gpu_config(c), [gpu_domain(c)], [q])
+    st = s.run(max_steps=5, check=False)
+    assert st["rc"] == fvna.ERR_NAN
+    s.close()
+
+
+# ------------------------------------------------------------------ FP32
+
+def test_fp32_perturbation_against_fp64_oracle():
+    """A smaller Gaussian pulse of the 2048^2 workload (same amplitude, width,
+    dx and parameters): FP32 perturbation path vs the FP64 oracle."""
+    w = wl.gaussian_2048(steps=300, n=192, seed=2)
+    c = Case(w.nx, w.ny, w.q0, bc=w.bc, beta=w.beta, delta=w.delta, dx=w.dx, nu_w=w.nu_w)
+    qo, so = run_oracle(c, 300)
+    qg, sg = run_gpu(c, 300, precision=fvna.FP32_PERT)
+    assert sg["rc"] == 0
+    peak, l2 = pressure_errors(qg[0] - 1.0, qo[0] - 1.0)
+    assert peak <= 1e-5 and l2 <= 1e-5, (peak, l2)
+    assert abs(sg["t"] - so["t"]) <= 1e-6 * so["t"]
+
+
+@pytest.mark.parametrize("bc", [(P, P, P, P), (R, E, T, E)])
+def test_fp32_borders_against_fp64(bc):
+    n = 96
+    q = wl.random_smooth(n, n, 1e-3, seed=57)
+    c = Case(n, n, q, bc=bc, beta=3.5, delta=2e-3, dx=1.0 / 24, taylor_ratio=1e-4, y0=0.0)
+    qo, _ = run_oracle(c, 100)
+    qg, sg = run_gpu(c, 100, precision=fvna.FP32_PERT)
+    assert sg["rc"] == 0
+    peak, l2 = pressure_errors(qg[0] - 1.0, qo[0] - 1.0)
+    assert peak <= 1e-5 and l2 <= 1e-5, (peak, l2)
