@@ -41,6 +41,7 @@ extern "C" {
 #define FVNA_ERR_NONREAL  -4  /* a Roe radicand was negative (section 3.2, S bound) */
 #define FVNA_ERR_CFL      -5  /* a step ran with nu > nu_max (section 4) */
 #define FVNA_ERR_NAN      -6  /* a wave speed was NaN */
+#define FVNA_ERR_SIZE     -7  /* domain larger than a fixed-size scratch area allows */
 
 /* ---- enumerations ------------------------------------------------------ */
 enum fvna_precision {
@@ -185,6 +186,35 @@ const char *fvna_strerror(int code);
  * radicand was negative (outputs are still written). */
 int fvna_riemann(int precision, double beta, int n, const double *qL, const double *qR,
                  double *s, double *W, double *amdq, double *apdq);
+
+/* fvna_step_noalloc -- one binary64 step that allocates no memory.  The paper
+ * has no counterpart: this is for callers that cannot allocate device memory
+ * at run time (an application that hands out all device memory up front, a
+ * locked-down allocator, a real-time loop that cannot afford cudaMalloc and
+ * its implicit synchronisation).
+ *   cfg       precision must be FVNA_FP64; geometry, limiter, sweeps, beta,
+ *             delta and dx are used, the CFL fields are not (dt is given)
+ *   dom       one domain (nx*ny <= FVNA_NOALLOC_MAX_CELLS)
+ *   q_in      device pointer, 3*nx*ny binary64 total variables in the layout
+ *             described at the top of this file (caller-owned, read only)
+ *   q_out     device pointer, same layout (caller-owned); may equal q_in
+ *   t, dt     time of the state and the step to take (driven borders use t)
+ *   smax_out  host pointer or NULL: receives max|s| of the step, for the
+ *             caller's own CFL rule (section 4)
+ *   stream    cudaStream_t to run on (NULL = legacy default stream)
+ * The intermediate planes and bookkeeping live in one file-scope device array
+ * of about 13 MB, which every GPU that loads this library keeps until the
+ * process exits.  The first call on a device looks that array up and sets the
+ * kernels' attributes, so make it before any stream capture; every call
+ * blocks until its step is done.  All calls share the array and each call
+ * clears what must start at zero, but calls that overlap on the GPU (two host
+ * threads, or several streams) race on it.  Results equal those of
+ * fvna_step with cfg->dt_fixed = dt.  Returns FVNA_OK, FVNA_ERR_ARG,
+ * FVNA_ERR_SIZE for a larger domain, FVNA_ERR_NONREAL / FVNA_ERR_NAN from the
+ * step, or FVNA_ERR_CUDA. */
+#define FVNA_NOALLOC_MAX_CELLS 524288
+int fvna_step_noalloc(const fvna_config *cfg, const fvna_domain *dom, const double *q_in,
+                      double *q_out, double t, double dt, double *smax_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -5,6 +5,7 @@ the static CUDA runtime:
   fvna_fp64.cu  binary64 kernels, -fmad=false (products never fused into sums)
   fvna_fp32.cu  binary32 perturbation kernels
   fvna_api.cu   host runtime behind include/fvna.h
+  fvna_noalloc.cu  the allocation-free binary64 step (fixed device scratch array)
 """
 from __future__ import annotations
 
@@ -24,6 +25,7 @@ UNITS = {
     "fvna_fp64": ["-fmad=false"],
     "fvna_fp32": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "fvna_api": [],
+    "fvna_noalloc": ["-fmad=false"],
 }
 
 

@@ -229,6 +229,7 @@ const char *fvna_strerror(int code) {
     case FVNA_ERR_NONREAL: return "non-real wave speeds (state outside the hyperbolic region)";
     case FVNA_ERR_CFL: return "CFL number above nu_max";
     case FVNA_ERR_NAN: return "NaN wave speed";
+    case FVNA_ERR_SIZE: return "domain larger than the fixed scratch area allows";
     default: return "unknown status";
   }
 }

@@ -25,6 +25,8 @@ BC_PERIODIC, BC_EXTRAP, BC_REFLECT, BC_TAYLOR, BC_HIFU = 0, 1, 2, 3, 4
 FIELD_Q, FIELD_PRESSURE, FIELD_BUDGET, FIELD_STATS = 0, 1, 2, 3
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONREAL, ERR_CFL, ERR_NAN = 0, -1, -2, -3, -4, -5, -6
+ERR_SIZE = -7
+NOALLOC_MAX_CELLS = 524288
 
 
 class FvnaError(RuntimeError):
@@ -63,7 +65,8 @@ class Stats(ctypes.Structure):
 
 
 SYMBOLS = ["fvna_init", "fvna_step", "fvna_run", "fvna_sync", "fvna_fields",
-           "fvna_step_timed", "fvna_launch_count", "fvna_destroy", "fvna_strerror", "fvna_riemann"]
+           "fvna_step_timed", "fvna_launch_count", "fvna_destroy", "fvna_strerror", "fvna_riemann",
+           "fvna_step_noalloc"]
 
 _lib = None
 
@@ -98,6 +101,9 @@ def lib():
     L.fvna_destroy.argtypes = [vp]
     L.fvna_strerror.restype = ctypes.c_char_p
     L.fvna_strerror.argtypes = [ctypes.c_int]
+    L.fvna_step_noalloc.restype = ctypes.c_int
+    L.fvna_step_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Domain), vp, vp,
+                                    ctypes.c_double, ctypes.c_double, dp, vp]
     L.fvna_riemann.restype = ctypes.c_int
     L.fvna_riemann.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, dp, dp]
     _lib = L
@@ -244,6 +250,22 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def step_noalloc(config: Config, domain: Domain, q_in, q_out, t: float, dt: float,
+                 stream=None):
+    """One binary64 step that allocates nothing (fvna_step_noalloc).
+
+    q_in, q_out: torch CUDA float64 tensors of shape (3, ny, nx) owned by the
+    caller (they may be the same tensor).  Returns (status, max|s|)."""
+    if stream is None:
+        stream = _current_stream()
+    sm = ctypes.c_double(0.0)
+    rc = lib().fvna_step_noalloc(ctypes.byref(config), ctypes.byref(domain),
+                                 ctypes.c_void_p(q_in.data_ptr()),
+                                 ctypes.c_void_p(q_out.data_ptr()), float(t), float(dt),
+                                 ctypes.byref(sm), ctypes.c_void_p(stream))
+    return rc, sm.value
 
 
 def riemann(precision: int, beta: float, qL, qR):
