@@ -56,9 +56,14 @@ def parse():
                     help="domain side (the headline is 2048; other sizes are for profiling)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", choices=["gaussian", "plane", "focused", "batched"],
+                    default="gaussian",
+                    help="gaussian: the headline line; the others print their own line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--plain-update", action="store_true",
+                    help="FP32 cell update as written instead of the compensated sum")
     ap.add_argument("--flush-mb", type=int, default=512,
                     help="L2 flush buffer written before every timed step (0: none)")
     return ap.parse_args()
@@ -219,10 +224,11 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def measure_precision(torch, fvna, w, precision, steps, warmup, flush, do_flush=True):
+def measure_precision(torch, fvna, w, precision, steps, warmup, flush, do_flush=True,
+                      compensated=1):
     stream = torch.cuda.current_stream()
     cfg = fvna.make_config(precision=precision, beta=w.beta, delta=w.delta, dx=w.dx,
-                           nu_w=w.nu_w, steps_per_graph=1)
+                           nu_w=w.nu_w, steps_per_graph=1, compensated=compensated)
     s = fvna.Solver(cfg, [fvna.make_domain(w.nx, w.ny, bc=w.bc)], [w.q0],
                     stream=stream.cuda_stream)
     for _ in range(warmup):
@@ -266,7 +272,8 @@ def run_native(args):
     torch.cuda.synchronize()
     with ClockSampler(dev_index) as clk:
         per, launches, st = measure_precision(torch, fvna, w, prec, args.steps, args.warmup,
-                                              flush, args.flush_mb > 0)
+                                              flush, args.flush_mb > 0,
+                                              0 if args.plain_update else 1)
     torch.cuda.synchronize()
     step_ms = per.sum(axis=1)
     total_s = float(step_ms.sum()) / 1e3
@@ -302,6 +309,7 @@ def run_native(args):
         "data": "synthetic",
         "config": {"workload": f"gaussian_pulse_{w.nx}x{w.ny}", "cells_per_gpu": cells,
                    "precision": args.precision, "time_steps_per_bench_step": 1,
+                   "compensated_update": (not args.plain_update) and args.precision == "fp32",
                    "l2": (f"flushed before every timed step ({args.flush_mb} MB write)"
                           if args.flush_mb > 0 else "not flushed"),
                    "parallelism": f"replicas x{world}"},
@@ -312,7 +320,7 @@ def run_native(args):
     }
 
     if not args.no_e2e:
-        line["e2e"] = e2e(torch, fvna, w, prec)
+        line["e2e"] = e2e(torch, fvna, w, prec, 0 if args.plain_update else 1)
     if prec == fvna.FP32_PERT and not args.no_fp64:
         per64, _, _ = measure_precision(torch, fvna, w, fvna.FP64, max(3, args.steps // 10), 2,
                                         flush, args.flush_mb > 0)
@@ -328,13 +336,13 @@ def run_native(args):
     return 0
 
 
-def e2e(torch, fvna, w, prec, reps=2):
+def e2e(torch, fvna, w, prec, compensated=1, reps=2):
     """Whole-run call sequence from pinned host memory, host wall clock."""
     cells = w.nx * w.ny
     q_host = torch.from_numpy(w.q0).pin_memory()
     out = torch.empty((3, w.ny, w.nx), dtype=torch.float64).pin_memory()
     cfg = fvna.make_config(precision=prec, beta=w.beta, delta=w.delta, dx=w.dx, nu_w=w.nu_w,
-                           steps_per_graph=64)
+                           steps_per_graph=64, compensated=compensated)
     times = []
     for _ in range(reps):
         torch.cuda.synchronize()
@@ -351,10 +359,156 @@ def e2e(torch, fvna, w, prec, reps=2):
             "time_steps_per_e2e_step": RUN_STEPS, "seconds": best}
 
 
+# ---------------------------------------------------------------- other workloads
+
+def _setup_cuda():
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1311_3004_gb300 import fvna
+    return torch, fvna
+
+
+def _timed(torch, fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def run_plane(args):
+    """512x8 plane-wave shock formation, FP64, 2000 steps (launch-bound: the
+    whole run is replayed from CUDA graphs)."""
+    torch, fvna = _setup_cuda()
+    w = wl.plane_wave_512x8()
+    cfg = fvna.make_config(precision=fvna.FP64, beta=w.beta, delta=w.delta, dx=w.dx, nu_w=w.nu_w,
+                           steps_per_graph=250)
+    dom = fvna.make_domain(w.nx, w.ny, bc=w.bc)
+    cfg, _ = fvna.autotune(cfg, [dom], [w.q0], trial_steps=20)   # small tiles for a tiny domain
+    cfg.steps_per_graph = 250
+    s = fvna.Solver(cfg, [dom], [w.q0])
+    s.run(max_steps=250)                      # warm-up (graph capture)
+    s.close()
+    s = fvna.Solver(cfg, [dom], [w.q0])
+    n0 = s.launch_count()
+    st, sec = _timed(torch, lambda: s.run(max_steps=w.steps))
+    launches = s.launch_count() - n0
+    s.close()
+    cells = w.nx * w.ny
+    print(json.dumps({"metric": METRIC, "value": cells * w.steps / sec, "unit": METRIC,
+                      "workload": w.name, "dtype": "f64", "steps": w.steps,
+                      "time_to_solution_s": sec, "us_per_step": 1e6 * sec / w.steps,
+                      "gpu_launches": launches, "t_end": st["t"],
+                      "tiles": [cfg.tile_x, cfg.tile_y]}), flush=True)
+    return 0
+
+
+def run_focused(args):
+    """Axisymmetric focused source, 4096x1024, ~8 focal transit times: FP32
+    perturbation path vs the plain FP64 path, time-to-solution and focal
+    peak pressure."""
+    torch, fvna = _setup_cuda()
+    w = wl.focused_axisym()
+    e = w.extra
+    dom = fvna.make_domain(w.nx, w.ny, bc=w.bc, envelope=e["envelope"], amp=e["amp"],
+                           focal=e["focal"], aperture=e["aperture"])
+    res = {}
+    for name, prec in (("fp32", fvna.FP32_PERT), ("fp64", fvna.FP64)):
+        cfg = fvna.make_config(precision=prec, geometry=fvna.AXISYMMETRIC, beta=w.beta,
+                               delta=w.delta, dx=w.dx, nu_w=w.nu_w, steps_per_graph=64)
+        s = fvna.Solver(cfg, [dom], [w.q0])
+        st, sec = _timed(torch, lambda: s.run(t_end=e["t_end"]))
+        p = s.pressure(0)
+        s.close()
+        res[name] = (st, sec, p)
+    cells = w.nx * w.ny
+    p32, p64 = res["fp32"][2], res["fp64"][2]
+    focal = float(np.max(p64)) * (wl.RHO0 * wl.C0 ** 2)
+    line = {"metric": METRIC, "unit": METRIC, "workload": w.name, "t_end": e["t_end"],
+            "value": cells * res["fp32"][0]["steps"] / res["fp32"][1], "dtype": "f32",
+            "fp32": {"steps": res["fp32"][0]["steps"], "time_to_solution_s": res["fp32"][1]},
+            "fp64": {"steps": res["fp64"][0]["steps"], "time_to_solution_s": res["fp64"][1],
+                     "value": cells * res["fp64"][0]["steps"] / res["fp64"][1]},
+            "speedup_vs_fp64": res["fp64"][1] / res["fp32"][1],
+            "focal_peak_pa_fp64": focal,
+            "focal_peak_rel_err": abs(float(np.max(p32)) - float(np.max(p64))) / float(np.max(p64)),
+            "l2_rel_err": float(np.linalg.norm(p32 - p64) / np.linalg.norm(p64))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batched(args):
+    """64 domains of uneven size in one context (one launch per sub-step over
+    all of them), FP32, autotuned tiles, 1000 steps each with its own dt;
+    against the plain FP64 solver looping over the domains one at a time
+    (timed over the first `fp64_steps` steps and scaled to 1000)."""
+    torch, fvna = _setup_cuda()
+    doms_in, beta, delta, dx = wl.batched_64()
+    steps, fp64_steps = 1000, 100
+    doms = [fvna.make_domain(nx, ny) for nx, ny, _, _ in doms_in]
+    qd = [torch.from_numpy(q).cuda() for _, _, q, _ in doms_in]
+    cells = sum(nx * ny for nx, ny, _, _ in doms_in)
+    cfg = fvna.make_config(precision=fvna.FP32_PERT, beta=beta, delta=delta, dx=dx, nu_w=0.9,
+                           steps_per_graph=50)
+    (best, ms_tune), tune_s = _timed(torch, lambda: fvna.autotune(cfg, doms, qd, trial_steps=10))
+    best.steps_per_graph = 50
+    s = fvna.Solver(best, doms, qd)
+    s.run(max_steps=5)
+    s.close()
+    s = fvna.Solver(best, doms, qd)
+    n0 = s.launch_count()
+    _, sec32 = _timed(torch, lambda: s.run(max_steps=steps))
+    launches = s.launch_count() - n0
+    s.close()
+    # plain FP64, one domain at a time, first fp64_steps steps
+    cfg64 = fvna.make_config(precision=fvna.FP64, beta=beta, delta=delta, dx=dx, nu_w=0.9,
+                             steps_per_graph=50)
+    errs = []
+
+    def plain():
+        for k, d in enumerate(doms):
+            s64 = fvna.Solver(cfg64, [d], [qd[k]])
+            s64.run(max_steps=fp64_steps)
+            s64.close()
+    _, sec64 = _timed(torch, plain)
+    # accuracy: FP32 batched vs FP64 per domain over fp64_steps steps (same t)
+    sb = fvna.Solver(best, doms, qd)
+    sb.run(max_steps=fp64_steps)
+    for k, d in enumerate(doms[:8]):
+        t_k = sb.stats(k)["t"]
+        s64 = fvna.Solver(cfg64, [d], [qd[k]])
+        s64.run(t_end=t_k, max_steps=10 * fp64_steps)
+        a, b = sb.pressure(k), s64.pressure(0)
+        errs.append(abs(float(np.max(np.abs(a))) - float(np.max(np.abs(b)))) / float(np.max(np.abs(b))))
+        s64.close()
+    sb.close()
+    line = {"metric": METRIC, "unit": METRIC, "workload": "batched_64_domains", "dtype": "f32",
+            "domains": len(doms), "cells": cells, "steps": steps,
+            "value": cells * steps / sec32, "time_to_solution_s": sec32,
+            "gpu_launches": launches,
+            "autotuned": {"tile_x": best.tile_x, "tile_y": best.tile_y, "ms_per_step": ms_tune,
+                          "tuning_s": tune_s},
+            "plain_fp64_sequential": {"value": cells * fp64_steps / sec64,
+                                      "time_to_solution_s_scaled": sec64 * steps / fp64_steps,
+                                      "measured_steps": fp64_steps},
+            "speedup_vs_plain_fp64": (sec64 * steps / fp64_steps) / sec32,
+            "peak_rel_err_vs_fp64_max": max(errs), "peak_err_domains": len(errs)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "plane":
+        return run_plane(args)
+    if args.workload == "focused":
+        return run_focused(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_native(args)
 
 

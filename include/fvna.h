@@ -84,9 +84,10 @@ typedef struct fvna_config {
   double nu_max;        /* a step with nu > nu_max ends the run with FVNA_ERR_CFL */
   double dt_fixed;      /* > 0: use this dt for every step instead of the CFL rule */
   int steps_per_graph;  /* steps captured per CUDA graph replay; 0 = default (32) */
-  int tile_x;           /* x1-sweep tile width (cells per warp row); 0 = default */
+  int tile_x;           /* x1-sweep tile width (16, 32 or 64 cells per warp row); 0 = default */
   int tile_y;           /* x2-sweep tile height (rows per warp); 0 = default */
-  int reserved;
+  int compensated;      /* FVNA_FP32_PERT: 1 = sum each cell update with error-free
+                           two-sums (one final rounding), 0 = as written */
 } fvna_config;
 
 /* One domain.  Coordinates are those of the lower-left corner of cell (0,0);
@@ -163,6 +164,18 @@ int fvna_fields(fvna_ctx *ctx, int domain, int what, void *dst, size_t bytes, in
  * sweep + source, ms[2] dt update.  The step is identical to one of
  * fvna_step.  Returns FVNA_OK or the device status after the step. */
 int fvna_step_timed(fvna_ctx *ctx, float ms[3]);
+
+/* fvna_autotune -- pick the sweep tile shapes for a set of domains.  Builds a
+ * throwaway context from the same arguments as fvna_init for each candidate
+ * (tile_x in {16, 32, 64}, tile_y in {8, 16, 32, 64, 128}), runs one warm-up graph of
+ * trial_steps steps and times a second one with CUDA events on `stream`,
+ * destroys it, and returns in *best a copy of *cfg with the fastest tile_x and
+ * tile_y (ms_per_step, if not NULL, receives its time per step).  The
+ * caller's q0 is only read.  Errors as fvna_init; FVNA_ERR_ARG if
+ * trial_steps < 1 or best is NULL. */
+int fvna_autotune(const fvna_config *cfg, int n_domains, const fvna_domain *doms,
+                  const double *const *q0, int q0_on_device, void *stream, int trial_steps,
+                  fvna_config *best, float *ms_per_step);
 
 /* fvna_launch_count -- kernels this context has enqueued so far (each kernel
  * node of a graph replay counts once). */

@@ -48,12 +48,17 @@
  *   -(1/r) (q3, z2 z3, z3^2)    with z = q / q1,
  * and uses the cylindrical vector Laplacian of the velocity for the viscous
  * part (axial: d_zz + d_rr + (1/r) d_r; radial: d_zz + d_rr + (1/r) d_r - 1/r^2).
+ * The two radial faces nearest the axis (r = 0 and r = dx) use the
+ * first-order flux: with the second-order correction there, the spectral
+ * radius of the linearised step exceeds one; with it removed the step is
+ * stable up to CFL 0.5 (measured on the linearised oracle step).
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
 #define NG 2
+#define AXIS_FACES 2  /* radial faces next to the axis with a first-order flux */
 
 enum { BC_PERIODIC = 0, BC_EXTRAP = 1, BC_REFLECT = 2, BC_TAYLOR = 3, BC_HIFU = 4 };
 enum { LIM_MC = 0, LIM_NONE = 1, LIM_LW = 2 };
@@ -94,6 +99,7 @@ typedef struct {
   double nu_min, nu_max_seen, nu_mean, nu_m2;   /* Welford running mean / M2 */
   long nu_count;
   int status;
+  int sweep_dir;       /* direction of the sweep in progress */
 } ora_state;
 
 /* max that propagates NaN, so that a NaN speed is never hidden */
@@ -299,6 +305,11 @@ static double sweep_line(ora_state *st, int n, double *line[3], double lam) {
     }
     /* limited correction flux, eq. limiter */
     double coef[3];
+    /* axisymmetric form: first-order (Godunov) flux on the radial faces at
+     * r = 0 and r = dx, where the split geometric source otherwise makes the
+     * second-order correction slightly unstable */
+    int axis_face = st->p.geometry == 1 && st->sweep_dir == 1 && st->p.y0 == 0.0 &&
+                    (m - NG) < AXIS_FACES;
     for (int p = 0; p < 3; p++) {
       int up = s[m][p] > 0.0 ? m - 1 : m + 1;
       double wdotw = W[m][p][0] * W[m][p][0] + W[m][p][1] * W[m][p][1] + W[m][p][2] * W[m][p][2];
@@ -306,7 +317,7 @@ static double sweep_line(ora_state *st, int n, double *line[3], double lam) {
       double theta = wdotw > 0.0 ? wup / wdotw : 0.0;
       double phi = wdotw > 0.0 ? limiter_phi(st->p.limiter, theta) : 0.0;
       double as = fabs(s[m][p]);
-      coef[p] = as * (1.0 - lam * as) * phi;
+      coef[p] = axis_face ? 0.0 : as * (1.0 - lam * as) * phi;
     }
     for (int k = 0; k < 3; k++)
       F[m][k] = 0.5 * (coef[0] * W[m][0][k] + coef[1] * W[m][1][k] + coef[2] * W[m][2][k]);
@@ -330,6 +341,7 @@ static double sweep(ora_state *st, int dir, double lam) {
   double *buf = malloc(sizeof(double) * 3 * (size_t)len);
   double *line[3] = {buf, buf + len, buf + 2 * len};
   double smax = 0.0;
+  st->sweep_dir = dir;
   for (int l = 0; l < lines; l++) {
     for (int c = 0; c < len; c++) {
       size_t id = dir == 0 ? idx(st, c - NG, l) : idx(st, l, c - NG);

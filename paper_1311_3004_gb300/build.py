@@ -44,7 +44,10 @@ def _stale() -> bool:
 
 def _compile(unit: str, verbose: bool) -> str:
     obj = os.path.join(OUT, unit + ".o")
-    cmd = [NVCC, *ARCH, *COMMON, *UNITS[unit], "-c", os.path.join(CSRC, unit + ".cu"), "-o", obj]
+    # FVNA_NVCC_FLAGS: extra flags (e.g. -DFVNA_MARCH_UNROLL=2) for tuning builds
+    extra = os.environ.get("FVNA_NVCC_FLAGS", "").split()
+    cmd = [NVCC, *ARCH, *COMMON, *UNITS[unit], *extra, "-c", os.path.join(CSRC, unit + ".cu"),
+           "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

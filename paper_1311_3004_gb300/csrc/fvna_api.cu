@@ -82,8 +82,9 @@ int validate(const fvna_config *c, int n, const fvna_domain *d, const double *co
   if (!(c->dt_fixed > 0.0) && !(c->nu_w > 0.0)) return FVNA_ERR_ARG;
   if (!(c->nu_max > 0.0)) return FVNA_ERR_ARG;
   if (c->steps_per_graph < 0 || c->steps_per_graph > 4096) return FVNA_ERR_ARG;
-  if (c->tile_x != 0 && c->tile_x != 32 && c->tile_x != 64) return FVNA_ERR_ARG;
+  if (c->tile_x != 0 && c->tile_x != 16 && c->tile_x != 32 && c->tile_x != 64) return FVNA_ERR_ARG;
   if (c->tile_y != 0 && (c->tile_y < 8 || c->tile_y > 4096)) return FVNA_ERR_ARG;
+  if (c->compensated != 0 && c->compensated != 1) return FVNA_ERR_ARG;
   for (int k = 0; k < n; k++) {
     const fvna_domain &D = d[k];
     if (D.nx < 1 || D.ny < 1 || D.nx > (1 << 20) || D.ny > (1 << 20)) return FVNA_ERR_ARG;
@@ -188,11 +189,15 @@ void fill_stats(const DomScal &S, fvna_stats *st) {
 // launch dispatch by precision
 // ---------------------------------------------------------------------------
 namespace fvna {
-cudaError_t prepare_kernels(int p, int tx) {
-  return p == FVNA_FP64 ? prepare_kernels_fp64(tx) : prepare_kernels_fp32(tx);
+cudaError_t prepare_kernels(int p, int tx, int lim, int comp) {
+  return p == FVNA_FP64 ? prepare_kernels_fp64(tx, lim, comp) : prepare_kernels_fp32(tx, lim, comp);
 }
-int occupancy_x(int p, int tx) { return p == FVNA_FP64 ? occupancy_x_fp64(tx) : occupancy_x_fp32(tx); }
-int occupancy_y(int p) { return p == FVNA_FP64 ? occupancy_y_fp64() : occupancy_y_fp32(); }
+int occupancy_x(int p, int tx, int lim, int comp) {
+  return p == FVNA_FP64 ? occupancy_x_fp64(tx, lim, comp) : occupancy_x_fp32(tx, lim, comp);
+}
+int occupancy_y(int p, int lim, int comp) {
+  return p == FVNA_FP64 ? occupancy_y_fp64(lim, comp) : occupancy_y_fp32(lim, comp);
+}
 cudaError_t launch_sweep_x(int p, int tx, const StepArgs &a, int b, cudaStream_t s) {
   return p == FVNA_FP64 ? launch_sweep_x_fp64(tx, a, b, s) : launch_sweep_x_fp32(tx, a, b, s);
 }
@@ -310,12 +315,13 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   CK(cudaMemcpyAsync(c->d_ty, ty.data(), sizeof(Tile) * ty.size(), cudaMemcpyHostToDevice, c->stream));
 
   // kernel set-up and persistent grid sizes
-  CK(prepare_kernels(prec, c->tile_x));
+  const int comp = prec == FVNA_FP32_PERT && cfg->compensated ? 1 : 0;
+  CK(prepare_kernels(prec, c->tile_x, cfg->limiter, comp));
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  int occx = std::max(1, occupancy_x(prec, c->tile_x));
-  int occy = std::max(1, occupancy_y(prec));
+  int occx = std::max(1, occupancy_x(prec, c->tile_x, cfg->limiter, comp));
+  int occy = std::max(1, occupancy_y(prec, cfg->limiter, comp));
   c->blocks_x = std::max(1, std::min((c->ntx + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, occx * sms));
   c->blocks_y = std::max(1, std::min((c->nty + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, occy * sms));
 
@@ -328,6 +334,7 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   a.nu_w = cfg->nu_w; a.nu_max = cfg->nu_max; a.dt_fixed = cfg->dt_fixed;
   a.limiter = cfg->limiter; a.geometry = cfg->geometry; a.sweeps = cfg->sweeps;
   a.tile_y = c->tile_y;
+  a.compensated = comp;
   c->args_x = a;
   c->args_x.tiles = c->d_tx;
   c->args_x.ntiles = c->ntx;
@@ -495,6 +502,60 @@ int fvna_step_timed(fvna_ctx *c, float ms[3]) {
   int rc = read_scal(c);
   if (rc != FVNA_OK) return rc;
   return first_status(c);
+}
+
+int fvna_autotune(const fvna_config *cfg, int n, const fvna_domain *doms, const double *const *q0,
+                  int q0_on_device, void *stream, int trial_steps, fvna_config *best,
+                  float *ms_per_step) {
+  if (!best || trial_steps < 1) return FVNA_ERR_ARG;
+  int v = validate(cfg, n, doms, q0);
+  if (v != FVNA_OK) return v;
+  static const int TX[3] = {16, 32, 64};
+  static const int TY[5] = {8, 16, 32, 64, 128};
+  float best_ms = -1.0f;
+  fvna_config winner = *cfg;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_err(ce);
+  }
+  int rc = FVNA_OK;
+  for (int a = 0; a < 3 && rc == FVNA_OK; a++)
+    for (int b = 0; b < 5 && rc == FVNA_OK; b++) {
+      fvna_config trial = *cfg;
+      trial.tile_x = TX[a];
+      trial.tile_y = TY[b];
+      trial.steps_per_graph = trial_steps;
+      fvna_ctx *c = new (std::nothrow) fvna_ctx();
+      if (!c) { rc = FVNA_ERR_OOM; break; }
+      rc = init_impl(&trial, n, doms, q0, q0_on_device, stream, c);
+      if (rc == FVNA_OK) rc = ensure_graph(c);
+      float ms = 0.0f;
+      for (int rep = 0; rep < 2 && rc == FVNA_OK; rep++) {  // warm-up, then timed
+        cudaError_t e = launch_prepare(c->args, -1e300, trial_steps, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(c->gexec, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) rc = cuda_err(e);
+      }
+      if (c->stream) cudaStreamSynchronize(c->stream);
+      free_ctx(c);
+      if (rc == FVNA_OK && (best_ms < 0.0f || ms < best_ms)) {
+        best_ms = ms;
+        winner = trial;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != FVNA_OK) return rc;
+  winner.steps_per_graph = cfg->steps_per_graph;
+  *best = winner;
+  if (ms_per_step) *ms_per_step = best_ms / (float)trial_steps;
+  return FVNA_OK;
 }
 
 long long fvna_launch_count(const fvna_ctx *c) { return c ? c->launches : 0; }

@@ -204,16 +204,8 @@ __device__ __forceinline__ bool roe(const P32 &, float beta2, float aL, float bL
   return nonreal;
 }
 
-template <class T> __device__ __forceinline__ T limiter_phi(int kind, T theta) {
-  if (kind == LIM_NONE) return T(0);
-  if (kind == LIM_LW) return T(1);
-  T a = T(0.5) * (T(1) + theta);
-  T m = a < T(2) ? a : T(2);
-  T b = T(2) * theta;
-  m = m < b ? m : b;
-  return m > T(0) ? m : T(0);
-}
-
+// Limiter function of eq. limiter for the ratio wup/wdotw; 0 when the wave is
+// zero (wdotw = 0).  LIM is the limiter kind (MC, none = Godunov, LW).
 template <class T> __device__ __forceinline__ T lim_ratio(T num, T den);
 template <> __device__ __forceinline__ double lim_ratio<double>(double num, double den) {
   return num / den;
@@ -222,29 +214,64 @@ template <> __device__ __forceinline__ float lim_ratio<float>(float num, float d
   return __fdividef(num, den);
 }
 
+template <int LIM, class T> __device__ __forceinline__ T limited(T wup, T wdotw) {
+  if (LIM == LIM_NONE) return T(0);
+  if (LIM == LIM_LW) return wdotw > T(0) ? T(1) : T(0);
+  T theta = lim_ratio<T>(wup, wdotw);
+  T a = T(0.5) * (T(1) + theta);
+  T m = a < T(2) ? a : T(2);
+  T b = T(2) * theta;
+  m = m < b ? m : b;
+  m = m > T(0) ? m : T(0);
+  return wdotw > T(0) ? m : T(0);
+}
+
 // Fluctuations (eqs. fluc:m, fluc:p) and the limited correction flux (eq.
-// limiter) of interface I, with the waves of its left (WL*) and right (WR*)
+// limiter) of interface I, with the waves of its left (Lf) and right (Rf)
 // neighbours for the upwind ratio theta.
 template <class T> struct FluxData {
   T am[3], ap[3], F[3];
 };
 
-template <class T>
+template <int LIM, class T>
+__device__ __forceinline__ T family_coef(T s, const T *W, const T *U, T lam) {
+  T wdotw = W[0] * W[0] + W[1] * W[1] + W[2] * W[2];
+  T wup = U[0] * W[0] + U[1] * W[1] + U[2] * W[2];
+  T phi = limited<LIM, T>(wup, wdotw);
+  T as = fabs(s);
+  return as * (T(1) - lam * as) * phi;
+}
+
+template <int LIM, class T>
 __device__ __forceinline__ void flux_data(const Iface<T> &I, const Iface<T> &Lf, const Iface<T> &Rf,
-                                          T lam, int lim, FluxData<T> &o) {
-  T sm0 = dmin0(I.s0), sm1 = dmin0(I.s1), sm2 = dmin0(I.s2);
-  T sp0 = dmax0(I.s0), sp1 = dmax0(I.s1), sp2 = dmax0(I.s2);
+                                          T lam, FluxData<T> &o) {
+  T coef0, coef1;
+  const T sm2 = dmin0(I.s2), sp2 = dmax0(I.s2);
+  if (I.s0 > T(0) && I.s1 < T(0)) {
+    // subsonic interface (always the case for acoustic perturbations): the
+    // first family moves right and the second left, so the sums over the
+    // families reduce to one term each (the dropped terms are exact zeros)
+    o.am[0] = I.s1 * I.W1[0];
+    o.am[1] = I.s1 * I.W1[1];
+    o.am[2] = I.s1 * I.W1[2] + sm2 * I.W2;
+    o.ap[0] = I.s0 * I.W0[0];
+    o.ap[1] = I.s0 * I.W0[1];
+    o.ap[2] = I.s0 * I.W0[2] + sp2 * I.W2;
+    coef0 = family_coef<LIM, T>(I.s0, I.W0, Lf.W0, lam);
+    coef1 = family_coef<LIM, T>(I.s1, I.W1, Rf.W1, lam);
+  } else {
+    T sm0 = dmin0(I.s0), sm1 = dmin0(I.s1);
+    T sp0 = dmax0(I.s0), sp1 = dmax0(I.s1);
 #pragma unroll
-  for (int k = 0; k < 2; k++) {
-    T am = T(0), ap = T(0);
-    am = am + sm0 * I.W0[k];
-    ap = ap + sp0 * I.W0[k];
-    am = am + sm1 * I.W1[k];
-    ap = ap + sp1 * I.W1[k];
-    o.am[k] = am;
-    o.ap[k] = ap;
-  }
-  {
+    for (int k = 0; k < 2; k++) {
+      T am = T(0), ap = T(0);
+      am = am + sm0 * I.W0[k];
+      ap = ap + sp0 * I.W0[k];
+      am = am + sm1 * I.W1[k];
+      ap = ap + sp1 * I.W1[k];
+      o.am[k] = am;
+      o.ap[k] = ap;
+    }
     T am = T(0), ap = T(0);
     am = am + sm0 * I.W0[2];
     ap = ap + sp0 * I.W0[2];
@@ -254,30 +281,13 @@ __device__ __forceinline__ void flux_data(const Iface<T> &I, const Iface<T> &Lf,
     ap = ap + sp2 * I.W2;
     o.am[2] = am;
     o.ap[2] = ap;
+    coef0 = family_coef<LIM, T>(I.s0, I.W0, I.s0 > T(0) ? Lf.W0 : Rf.W0, lam);
+    coef1 = family_coef<LIM, T>(I.s1, I.W1, I.s1 > T(0) ? Lf.W1 : Rf.W1, lam);
   }
-  // family 1
-  T coef0, coef1, coef2;
-  {
-    const T *U = I.s0 > T(0) ? Lf.W0 : Rf.W0;
-    T wdotw = I.W0[0] * I.W0[0] + I.W0[1] * I.W0[1] + I.W0[2] * I.W0[2];
-    T wup = U[0] * I.W0[0] + U[1] * I.W0[1] + U[2] * I.W0[2];
-    T phi = wdotw > T(0) ? limiter_phi<T>(lim, lim_ratio<T>(wup, wdotw)) : T(0);
-    T as = fabs(I.s0);
-    coef0 = as * (T(1) - lam * as) * phi;
-  }
-  {
-    const T *U = I.s1 > T(0) ? Lf.W1 : Rf.W1;
-    T wdotw = I.W1[0] * I.W1[0] + I.W1[1] * I.W1[1] + I.W1[2] * I.W1[2];
-    T wup = U[0] * I.W1[0] + U[1] * I.W1[1] + U[2] * I.W1[2];
-    T phi = wdotw > T(0) ? limiter_phi<T>(lim, lim_ratio<T>(wup, wdotw)) : T(0);
-    T as = fabs(I.s1);
-    coef1 = as * (T(1) - lam * as) * phi;
-  }
+  T coef2;
   {
     T U = I.s2 > T(0) ? Lf.W2 : Rf.W2;
-    T wdotw = I.W2 * I.W2;
-    T wup = U * I.W2;
-    T phi = wdotw > T(0) ? limiter_phi<T>(lim, lim_ratio<T>(wup, wdotw)) : T(0);
+    T phi = limited<LIM, T>(U * I.W2, I.W2 * I.W2);
     T as = fabs(I.s2);
     coef2 = as * (T(1) - lam * as) * phi;
   }
@@ -287,27 +297,32 @@ __device__ __forceinline__ void flux_data(const Iface<T> &I, const Iface<T> &Lf,
 }
 
 // Cell update of eq. fv-hr.  binary64: evaluated as written.
+template <bool COMP>
 __device__ __forceinline__ double cell_update(const P64 &, double q, double am_r, double ap_l,
                                               double F_r, double F_l, double lam) {
   return q - lam * (am_r + ap_l) - lam * (F_r - F_l);
 }
 
-// binary32: the old value and the four flux terms are summed with error-free
-// two-sums (Knuth), so the new value is rounded once from the exact sum of
-// the rounded terms (compensated summation of the flux-difference update).
+// binary32 with COMP: the two increments of eq. fv-hr (fluctuations and the
+// correction-flux difference) are added to the old value with error-free
+// two-sums (Knuth) and their rounding errors folded back once (Neumaier), so
+// the new value is rounded once from the exact sum of the two increments.
+// Without COMP the update is evaluated as written.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = a + b;
   float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
 }
+template <bool COMP>
 __device__ __forceinline__ float cell_update(const P32 &, float q, float am_r, float ap_l,
                                              float F_r, float F_l, float lam) {
-  float s, e, c;
-  two_sum(q, -lam * am_r, s, c);
-  two_sum(s, -lam * ap_l, s, e); c += e;
-  two_sum(s, -lam * F_r, s, e); c += e;
-  two_sum(s, lam * F_l, s, e); c += e;
-  return s + c;
+  if (!COMP) return q - lam * (am_r + ap_l) - lam * (F_r - F_l);
+  float t1 = -lam * (am_r + ap_l);
+  float t2 = -lam * (F_r - F_l);
+  float s, e1, e2;
+  two_sum(q, t1, s, e1);
+  two_sum(s, t2, s, e2);
+  return s + (e1 + e2);
 }
 
 // ---------------------------------------------------------------------------

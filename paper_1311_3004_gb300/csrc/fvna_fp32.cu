@@ -4,4 +4,5 @@
 
 #define POLICY P32
 #define SUFFIX fp32
+#define HAS_COMP 1
 #include "fvna_precision.inc"

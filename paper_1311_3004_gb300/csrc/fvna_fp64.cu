@@ -10,9 +10,21 @@
 
 #define POLICY P64
 #define SUFFIX fp64
+#define HAS_COMP 0
 #include "fvna_precision.inc"
 
 namespace fvna {
+
+// Constants of one step derived from dt, evaluated once per domain and step
+// (dt/dx for the sweeps, dt*delta/dx^2 for the source), in binary64 and
+// rounded to binary32 for the perturbation kernels.
+__device__ __forceinline__ void set_step_scalars(DomScal *S, const StepArgs &A) {
+  S->lam = S->dt / A.dx;
+  S->coef = S->dt * A.delta / (A.dx * A.dx);
+  S->lam32 = (float)S->lam;
+  S->coef32 = (float)S->coef;
+  S->dt32 = (float)S->dt;
+}
 
 // End of a step for every domain: CFL number of the step just taken, the
 // CFL statistics (Welford), dt of the next step (nu_W dx / max|s|), time,
@@ -63,6 +75,7 @@ __global__ void k_advance(StepArgs A) {
     S->dt = S->t_end - S->t;
     S->last = 1;
   }
+  set_step_scalars(S, A);
 }
 
 // Start of a run: time limit and step budget, dt of the first step.
@@ -90,6 +103,7 @@ __global__ void k_prepare(StepArgs A, double t_end, long long max_steps) {
     S->dt = S->t_end - S->t;
     S->last = 1;
   }
+  set_step_scalars(S, A);
 }
 
 // After the speed-only pass over the initial state: dt_0 = nu_W dx / max|s|.
@@ -108,6 +122,7 @@ __global__ void k_first_dt(StepArgs A) {
   S->smax_bits = 0ull;
   S->status_bits = 0;
   S->nu_min = 1e300;
+  set_step_scalars(S, A);
 }
 
 cudaError_t launch_advance(const StepArgs &a, cudaStream_t s) {

@@ -14,10 +14,10 @@ constexpr int YRING = 8;  // rows in flight per warp in the x2 sweep
 size_t smem_sweep_x(int precision, int tile_x);
 size_t smem_sweep_y(int precision);
 // one-time attribute setup (opt-in shared memory); returns cudaSuccess or the error
-cudaError_t prepare_kernels(int precision, int tile_x);
+cudaError_t prepare_kernels(int precision, int tile_x, int lim, int comp);
 // resident blocks per SM of each sweep
-int occupancy_x(int precision, int tile_x);
-int occupancy_y(int precision);
+int occupancy_x(int precision, int tile_x, int lim, int comp);
+int occupancy_y(int precision, int lim, int comp);
 
 cudaError_t launch_sweep_x(int precision, int tile_x, const StepArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_sweep_y(int precision, const StepArgs &a, int blocks, cudaStream_t s);
@@ -39,9 +39,9 @@ cudaError_t launch_import_fp64(const DomDev &d, const double *q0, cudaStream_t s
 cudaError_t launch_export_fp64(const DomDev &d, double *out, int what, cudaStream_t s);
 cudaError_t launch_riemann_fp64(double beta, int n, const double *qL, const double *qR, double *s,
                                 double *W, double *am, double *ap, int *nonreal, cudaStream_t st);
-cudaError_t prepare_kernels_fp64(int tile_x);
-int occupancy_x_fp64(int tile_x);
-int occupancy_y_fp64();
+cudaError_t prepare_kernels_fp64(int tile_x, int lim, int comp);
+int occupancy_x_fp64(int tile_x, int lim, int comp);
+int occupancy_y_fp64(int lim, int comp);
 
 cudaError_t launch_sweep_x_fp32(int tile_x, const StepArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_sweep_y_fp32(const StepArgs &a, int blocks, cudaStream_t s);
@@ -50,8 +50,8 @@ cudaError_t launch_import_fp32(const DomDev &d, const double *q0, cudaStream_t s
 cudaError_t launch_export_fp32(const DomDev &d, double *out, int what, cudaStream_t s);
 cudaError_t launch_riemann_fp32(double beta, int n, const double *qL, const double *qR, double *s,
                                 double *W, double *am, double *ap, int *nonreal, cudaStream_t st);
-cudaError_t prepare_kernels_fp32(int tile_x);
-int occupancy_x_fp32(int tile_x);
-int occupancy_y_fp32();
+cudaError_t prepare_kernels_fp32(int tile_x, int lim, int comp);
+int occupancy_x_fp32(int tile_x, int lim, int comp);
+int occupancy_y_fp32(int lim, int comp);
 
 }  // namespace fvna

@@ -52,6 +52,18 @@ std::mutex g_mutex;
 void *g_addr[256] = {};
 int g_blocks_x[256] = {}, g_blocks_y[256] = {};
 
+typedef void (*StepKernel)(StepArgs);
+StepKernel kx(int lim) {
+  if (lim == LIM_NONE) return k_sweep_x<P64, TILE_X, LIM_NONE, false>;
+  if (lim == LIM_LW) return k_sweep_x<P64, TILE_X, LIM_LW, false>;
+  return k_sweep_x<P64, TILE_X, LIM_MC, false>;
+}
+StepKernel ky(int lim) {
+  if (lim == LIM_NONE) return k_sweep_y<P64, YRING, LIM_NONE, false>;
+  if (lim == LIM_LW) return k_sweep_y<P64, YRING, LIM_LW, false>;
+  return k_sweep_y<P64, YRING, LIM_MC, false>;
+}
+
 int setup_device(int dev) {
   std::lock_guard<std::mutex> lock(g_mutex);
   if (g_addr[dev]) return FVNA_OK;
@@ -59,19 +71,19 @@ int setup_device(int dev) {
   if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return FVNA_ERR_CUDA;
   size_t smx = (size_t)WARPS_PER_BLOCK * 3 * XROWS * (TILE_X + 2 * HALO_X + 1) * sizeof(double);
   size_t smy = (size_t)WARPS_PER_BLOCK * YRING * 96 * sizeof(double);
-  if (cudaFuncSetAttribute(k_sweep_x<P64, TILE_X>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smx) != cudaSuccess)
-    return FVNA_ERR_CUDA;
-  if (cudaFuncSetAttribute(k_sweep_y<P64, YRING>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smy) != cudaSuccess)
-    return FVNA_ERR_CUDA;
+  for (int lim = 0; lim < 3; lim++) {
+    if (cudaFuncSetAttribute(kx(lim), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smx) !=
+        cudaSuccess)
+      return FVNA_ERR_CUDA;
+    if (cudaFuncSetAttribute(ky(lim), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy) !=
+        cudaSuccess)
+      return FVNA_ERR_CUDA;
+  }
   int sms = 0, ox = 0, oy = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return FVNA_ERR_CUDA;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ox, k_sweep_x<P64, TILE_X>,
-                                                WARPS_PER_BLOCK * 32, smx);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oy, k_sweep_y<P64, YRING>,
-                                                WARPS_PER_BLOCK * 32, smy);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ox, kx(LIM_MC), WARPS_PER_BLOCK * 32, smx);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oy, ky(LIM_MC), WARPS_PER_BLOCK * 32, smy);
   g_blocks_x[dev] = (ox > 0 ? ox : 1) * sms;
   g_blocks_y[dev] = (oy > 0 ? oy : 1) * sms;
   g_addr[dev] = p;
@@ -136,6 +148,12 @@ extern "C" int fvna_step_noalloc(const fvna_config *cfg, const fvna_domain *dom,
   sc.dt = dt;
   sc.dt_cfl = dt;
   sc.done = 0;
+  // the same expressions as the device's per-step constants
+  sc.lam = dt / cfg->dx;
+  sc.coef = dt * cfg->delta / (cfg->dx * cfg->dx);
+  sc.lam32 = (float)sc.lam;
+  sc.coef32 = (float)sc.coef;
+  sc.dt32 = (float)dt;
 
   // warp tiles (written into the scratch array from this host stack buffer
   // in chunks, so no host allocation either)
@@ -197,10 +215,10 @@ extern "C" int fvna_step_noalloc(const fvna_config *cfg, const fvna_domain *dom,
   by = by < g_blocks_y[dev] ? by : g_blocks_y[dev];
   size_t smx = (size_t)WARPS_PER_BLOCK * 3 * XROWS * (TILE_X + 2 * HALO_X + 1) * sizeof(double);
   size_t smy = (size_t)WARPS_PER_BLOCK * YRING * 96 * sizeof(double);
-  k_sweep_x<P64, TILE_X><<<bx, WARPS_PER_BLOCK * 32, smx, st>>>(ax);
+  kx(cfg->limiter)<<<bx, WARPS_PER_BLOCK * 32, smx, st>>>(ax);
   e = cudaGetLastError();
   if (e == cudaSuccess) {
-    k_sweep_y<P64, YRING><<<by, WARPS_PER_BLOCK * 32, smy, st>>>(ay);
+    ky(cfg->limiter)<<<by, WARPS_PER_BLOCK * 32, smy, st>>>(ay);
     e = cudaGetLastError();
   }
   DomScal out;

@@ -18,6 +18,21 @@
 
 #include "fvna_device.cuh"
 
+// Tuning knobs (compile-time): unroll factor of the line march's steady loop
+// and the minimum resident blocks per SM requested from the register
+// allocator for each sweep.
+#ifndef FVNA_MARCH_UNROLL
+#define FVNA_MARCH_UNROLL 0   // 0: leave the choice to the compiler
+#endif
+#ifndef FVNA_X_MINBLOCKS
+#define FVNA_X_MINBLOCKS 1
+#endif
+#ifndef FVNA_Y_MINBLOCKS
+#define FVNA_Y_MINBLOCKS 4    // 128 registers: 16 warps per SM (measured 25 % faster than 12)
+#endif
+#define FVNA_PRAGMA(x) _Pragma(#x)
+#define FVNA_UNROLL(n) FVNA_PRAGMA(unroll n)
+
 namespace fvna {
 
 // ---------------------------------------------------------------------------
@@ -106,20 +121,51 @@ __device__ __forceinline__ bool x_driven(const DomDev &D, int gx, int gy, double
 // updated and handed to sink.put(c, a, b, cc).  Faces k in [klo, khi] count
 // towards max|s|; interfaces in [nlo, nhi] towards the non-real flag.
 // ---------------------------------------------------------------------------
-// running max of |s| in the working precision; once NaN it stays NaN
-template <class T> __device__ __forceinline__ void smax_upd(T &m, T a) {
-  m = (a != a || a > m) ? a : m;
-}
-template <class T> __device__ __forceinline__ void speed_max(T &smax, const Iface<T> &I) {
-  smax_upd(smax, fabs(I.s0));
-  smax_upd(smax, fabs(I.s1));
-  smax_upd(smax, fabs(I.s2));
+// Running max of |s| kept as the bit pattern of |s|: for non-negative IEEE
+// values the pattern orders like an unsigned integer and a NaN (positive
+// sign) sorts above +inf, so the max cannot hide a NaN.  |s3| = |u| never
+// exceeds max(|s1|, |s2|) = max(|u + c|, |u - c|) for c >= 0 (rounding is
+// monotone), so two families suffice.
+template <class T> struct SpeedBits;
+template <> struct SpeedBits<float> {
+  typedef unsigned int U;
+  __device__ static __forceinline__ U bits(float s) { return __float_as_uint(s) & 0x7fffffffu; }
+  __device__ static __forceinline__ double value(U b) { return (double)__uint_as_float(b); }
+  __device__ static __forceinline__ U warp_max(U b) { return __reduce_max_sync(0xffffffffu, b); }
+};
+template <> struct SpeedBits<double> {
+  typedef unsigned long long U;
+  __device__ static __forceinline__ U bits(double s) {
+    return (unsigned long long)__double_as_longlong(s) & 0x7fffffffffffffffull;
+  }
+  __device__ static __forceinline__ double value(U b) { return __longlong_as_double((long long)b); }
+  __device__ static __forceinline__ U warp_max(U b) {
+    for (int o = 16; o > 0; o >>= 1) {
+      U v = __shfl_xor_sync(0xffffffffu, b, o);
+      b = v > b ? v : b;
+    }
+    return b;
+  }
+};
+template <class T>
+__device__ __forceinline__ void speed_max(typename SpeedBits<T>::U &m, const Iface<T> &I) {
+  typename SpeedBits<T>::U b0 = SpeedBits<T>::bits(I.s0), b1 = SpeedBits<T>::bits(I.s1);
+  m = b0 > m ? b0 : m;
+  m = b1 > m ? b1 : m;
 }
 
-template <class P, class Src, class Sink>
+// Interfaces in [glo, ghi] get the first-order flux (no correction term).
+template <class T> __device__ __forceinline__ void first_order(FluxData<T> &f) {
+  f.F[0] = T(0);
+  f.F[1] = T(0);
+  f.F[2] = T(0);
+}
+
+template <class P, int LIM, bool COMP, class Src, class Sink>
 __device__ __forceinline__ void march(Src &src, Sink &sink, int ncells, typename P::T beta2,
-                                      typename P::T lam, int lim, int klo, int khi, int nlo,
-                                      int nhi, typename P::T &smax, bool &nonreal) {
+                                      typename P::T lam, int klo, int khi, int nlo, int nhi,
+                                      typename SpeedBits<typename P::T>::U &smax, bool &nonreal,
+                                      int glo = 1, int ghi = 0) {
   typedef typename P::T T;
   T a0, b0, c0;        // cell c-2 (old)
   T a1, b1, c1;        // cell c-1 (old)
@@ -148,11 +194,15 @@ __device__ __forceinline__ void march(Src &src, Sink &sink, int ncells, typename
     if (c == 2) Ib = I;
     if (c == 3) Ic = I;
   }
-  flux_data<T>(Ib, Ia, Ic, lam, lim, Fl);
-  if (2 >= klo && 2 <= khi) speed_max(smax, Ib);
+  flux_data<LIM, T>(Ib, Ia, Ic, lam, Fl);
+  if (2 >= glo && 2 <= ghi) first_order(Fl);
+  if (2 >= klo && 2 <= khi) speed_max<T>(smax, Ib);
   Ia = Ib;
   Ib = Ic;
   // now a0.. = cell 2, a1.. = cell 3
+#if FVNA_MARCH_UNROLL > 0
+  FVNA_UNROLL(FVNA_MARCH_UNROLL)
+#endif
   for (int c = 4; c < ncells; c++) {
     T a, b, cc;
     src.get(c, a, b, cc);
@@ -161,11 +211,12 @@ __device__ __forceinline__ void march(Src &src, Sink &sink, int ncells, typename
     bool nr = roe(P(), beta2, a1, b1, c1, zb1, zc1, a, b, cc, zb, zc, Ic);
     if (c >= nlo && c <= nhi) nonreal |= nr;
     // interface c-1 is the right face of cell c-2
-    flux_data<T>(Ib, Ia, Ic, lam, lim, Fr);
-    if (c - 1 >= klo && c - 1 <= khi) speed_max(smax, Ib);
-    T na = cell_update(P(), a0, Fr.am[0], Fl.ap[0], Fr.F[0], Fl.F[0], lam);
-    T nb = cell_update(P(), b0, Fr.am[1], Fl.ap[1], Fr.F[1], Fl.F[1], lam);
-    T nc = cell_update(P(), c0, Fr.am[2], Fl.ap[2], Fr.F[2], Fl.F[2], lam);
+    flux_data<LIM, T>(Ib, Ia, Ic, lam, Fr);
+    if (c - 1 >= glo && c - 1 <= ghi) first_order(Fr);
+    if (c - 1 >= klo && c - 1 <= khi) speed_max<T>(smax, Ib);
+    T na = cell_update<COMP>(P(), a0, Fr.am[0], Fl.ap[0], Fr.F[0], Fl.F[0], lam);
+    T nb = cell_update<COMP>(P(), b0, Fr.am[1], Fl.ap[1], Fr.F[1], Fl.F[1], lam);
+    T nc = cell_update<COMP>(P(), c0, Fr.am[2], Fl.ap[2], Fr.F[2], Fl.F[2], lam);
     sink.put(c - 2, na, nb, nc);
     Ia = Ib;
     Ib = Ic;
@@ -210,8 +261,8 @@ template <class T> struct SmemRowSink {
   }
 };
 
-template <class P, int TX>
-__global__ void __launch_bounds__(128) k_sweep_x(StepArgs A) {
+template <class P, int TX, int LIM, bool COMP>
+__global__ void __launch_bounds__(128, FVNA_X_MINBLOCKS) k_sweep_x(StepArgs A) {
   typedef typename P::T T;
   constexpr int NC = TX + 2 * HALO_X;
   constexpr int PITCH = NC + 1;             // odd: a column read by 32 lanes is conflict-free
@@ -228,8 +279,8 @@ __global__ void __launch_bounds__(128) k_sweep_x(StepArgs A) {
     const DomDev &D = A.doms[tl.dom];
     DomScal *S = A.scal + tl.dom;
     if (S->done) continue;
-    const double dt = S->dt, t = S->t;
-    const T lam = (T)(dt / A.dx);
+    const double t = S->t;
+    const T lam = P::pert ? (T)S->lam32 : (T)S->lam;
     const int nx = D.nx, ny = D.ny;
     const T *qi[3] = {(const T *)D.qa[0], (const T *)D.qa[1], (const T *)D.qa[2]};
     T *qo[3] = {(T *)D.qb[0], (T *)D.qb[1], (T *)D.qb[2]};
@@ -259,7 +310,7 @@ __global__ void __launch_bounds__(128) k_sweep_x(StepArgs A) {
     cp_wait<0>();
     __syncwarp();
 
-    T smax = T(0);
+    typename SpeedBits<T>::U smax = 0;
     bool nonreal = false;
     // with the x1 sweep off the tile is stored unchanged
     if (xsweep && tl.y0 + lane < ny) {
@@ -268,7 +319,7 @@ __global__ void __launch_bounds__(128) k_sweep_x(StepArgs A) {
       SmemRowSink<T> sink{row, FS, nx - tl.x0 + HALO_X - 1};
       int khi = min(TX + HALO_X, nx - tl.x0 + HALO_X);
       int nhi = min(NC - 1, nx + 1 - (tl.x0 - HALO_X));
-      march<P>(src, sink, NC, beta2, lam, A.limiter, HALO_X, khi, 1, nhi, smax, nonreal);
+      march<P, LIM, COMP>(src, sink, NC, beta2, lam, HALO_X, khi, 1, nhi, smax, nonreal);
     }
     __syncwarp();
 
@@ -284,10 +335,10 @@ __global__ void __launch_bounds__(128) k_sweep_x(StepArgs A) {
         qo[2][off] = s[2 * FS];
       }
     }
-    double sm64 = warp_max((double)smax);
+    smax = SpeedBits<T>::warp_max(smax);
     int nr = warp_or(nonreal ? 1 : 0);
     if (lane == 0) {
-      atomic_max_speed(&S->smax_bits, sm64);
+      atomic_max_speed(&S->smax_bits, SpeedBits<T>::value(smax));
       if (nr) atomicOr(&S->status_bits, ST_NONREAL);
     }
     __syncwarp();
@@ -336,6 +387,21 @@ template <class P, int RING> struct RingSrc {
   }
 };
 
+// Warp sum of (partial sum, rounding error) pairs: binary64 adds it directly;
+// binary32 combines the pairs with two-sums and converts once on the result.
+__device__ __forceinline__ double warp_sum_pair(double s, double e) { return warp_sum(s + e); }
+__device__ __forceinline__ double warp_sum_pair(float s, float e) {
+  for (int o = 16; o > 0; o >>= 1) {
+    float so = __shfl_xor_sync(0xffffffffu, s, o);
+    float eo = __shfl_xor_sync(0xffffffffu, e, o);
+    float t = s + so;
+    float bb = t - s;
+    e = e + eo + ((s - (t - bb)) + (so - bb));
+    s = t;
+  }
+  return (double)s + (double)e;
+}
+
 template <class P> struct YSink {
   typedef typename P::T T;
   const DomDev *D;
@@ -346,11 +412,15 @@ template <class P> struct YSink {
   T coef, dtT;
   // post-x2-sweep row e-1 and the velocities z of rows e-1, e-2
   T qp0, qp1, qp2, zp2, zp3, zpp2, zpp3;
-  // per-lane budget partial sums with their rounding errors (two-sum), so
-  // the binary64 totals do not depend on binary32 accumulation order
+  // per-lane budget partial sums; in binary32 with their rounding errors
+  // (two-sum), so the binary64 totals keep the precision of binary64 sums
   T bud[3], bude[3];
 
   __device__ __forceinline__ void acc(int k, T x) {
+    if (!P::pert) {
+      bud[k] += x;
+      return;
+    }
     T s = bud[k] + x;
     T bb = s - bud[k];
     bude[k] += (bud[k] - (s - bb)) + (x - bb);
@@ -442,8 +512,8 @@ template <class P> struct YSink {
   }
 };
 
-template <class P, int RING>
-__global__ void __launch_bounds__(128) k_sweep_y(StepArgs A) {
+template <class P, int RING, int LIM, bool COMP>
+__global__ void __launch_bounds__(128, FVNA_Y_MINBLOCKS) k_sweep_y(StepArgs A) {
   typedef typename P::T T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -459,7 +529,7 @@ __global__ void __launch_bounds__(128) k_sweep_y(StepArgs A) {
     DomScal *S = A.scal + tl.dom;
     if (S->done) continue;
     const double dt = S->dt, t = S->t;
-    const T lam = (T)(dt / A.dx);
+    const T lam = P::pert ? (T)S->lam32 : (T)S->lam;
     const int nx = D.nx, ny = D.ny;
     const int TY = A.tile_y;
     const int ncells = TY + 2 * HALO_Y;
@@ -495,33 +565,38 @@ __global__ void __launch_bounds__(128) k_sweep_y(StepArgs A) {
     sink.D = &D; sink.qo = qo; sink.lane = lane; sink.gx = gx; sink.y0 = tl.y0;
     sink.tile_y = TY; sink.upd_lane = upd_lane; sink.xdrv = xdrv; sink.source = source;
     sink.axi = A.geometry == 1; sink.t = t; sink.dx = A.dx; sink.dt = dt;
-    sink.coef = (T)(dt * A.delta / (A.dx * A.dx));
-    sink.dtT = (T)dt;
+    sink.coef = P::pert ? (T)S->coef32 : (T)S->coef;
+    sink.dtT = P::pert ? (T)S->dt32 : (T)dt;
     sink.qp0 = sink.qp1 = sink.qp2 = T(0);
     sink.zp2 = sink.zp3 = sink.zpp2 = sink.zpp3 = T(0);
     for (int k = 0; k < 3; k++) sink.bud[k] = sink.bude[k] = T(0);
 
-    T smax = T(0);
+    typename SpeedBits<T>::U smax = 0;
     bool nonreal = false;
     // faces of this tile's cells (k = 3 is face y0), and the interfaces the
     // reference sweep computes (faces -1..ny+1), for in-domain lanes only
     int klo = HALO_Y, khi = min(TY + HALO_Y, ny - tl.y0 + HALO_Y);
     int nlo = max(1, 2 - tl.y0), nhi = ny + 4 - tl.y0;
     if (!upd_lane) { klo = 1; khi = 0; nlo = 1; nhi = 0; }
+    // axisymmetric form: first-order flux on the radial faces at r = 0 and
+    // r = dx (faces 0 and 1, local interfaces 3 and 4 of the first row tile)
+    int glo = 1, ghi = 0;
+    if (A.geometry == 1 && D.y0 == 0.0 && tl.y0 == 0) { glo = HALO_Y; ghi = HALO_Y + AXIS_FACES - 1; }
     if (ysweep)
-      march<P>(src, sink, ncells, beta2, lam, A.limiter, klo, khi, nlo, nhi, smax, nonreal);
+      march<P, LIM, COMP>(src, sink, ncells, beta2, lam, klo, khi, nlo, nhi, smax, nonreal, glo,
+                          ghi);
     else
       march_copy<P>(src, sink, ncells);
     cp_wait<0>();
     __syncwarp();
 
-    double sm64 = warp_max((double)smax);
+    smax = SpeedBits<T>::warp_max(smax);
     int nr = warp_or(nonreal ? 1 : 0);
-    double b0 = warp_sum((double)sink.bud[0] + (double)sink.bude[0]);
-    double b1 = warp_sum((double)sink.bud[1] + (double)sink.bude[1]);
-    double b2 = warp_sum((double)sink.bud[2] + (double)sink.bude[2]);
+    double b0 = warp_sum_pair(sink.bud[0], sink.bude[0]);
+    double b1 = warp_sum_pair(sink.bud[1], sink.bude[1]);
+    double b2 = warp_sum_pair(sink.bud[2], sink.bude[2]);
     if (lane == 0) {
-      atomic_max_speed(&S->smax_bits, sm64);
+      atomic_max_speed(&S->smax_bits, SpeedBits<T>::value(smax));
       if (nr) atomicOr(&S->status_bits, ST_NONREAL);
       atomicAdd(&S->budget_acc[0], b0);
       atomicAdd(&S->budget_acc[1], b1);
@@ -543,7 +618,7 @@ __global__ void k_speeds(StepArgs A, int dom, int use_b) {
   for (int k = 0; k < 3; k++) q[k] = (const T *)(use_b ? D.qb[k] : D.qa[k]);
   const long long nxf = (long long)(D.nx + 1) * D.ny;
   const long long nyf = (long long)D.nx * (D.ny + 1);
-  T smax = T(0);
+  typename SpeedBits<T>::U smax = 0;
   bool nonreal = false;
   for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nxf + nyf;
        f += (long long)gridDim.x * blockDim.x) {
@@ -567,12 +642,12 @@ __global__ void k_speeds(StepArgs A, int dom, int use_b) {
                R[1] * rr, I);
     }
     nonreal |= nr;
-    speed_max(smax, I);
+    speed_max<T>(smax, I);
   }
-  double sm64 = warp_max((double)smax);
+  smax = SpeedBits<T>::warp_max(smax);
   int nr = warp_or(nonreal ? 1 : 0);
   if ((threadIdx.x & 31) == 0) {
-    atomic_max_speed(&S->smax_bits, sm64);
+    atomic_max_speed(&S->smax_bits, SpeedBits<T>::value(smax));
     if (nr) atomicOr(&S->status_bits, ST_NONREAL);
   }
 }
@@ -634,7 +709,7 @@ __global__ void k_riemann(double beta, int n, const double *qL, const double *qR
                 R[2], R[1] * rr, R[2] * rr, I);
   if (nr) atomicOr(nonreal, 1);
   FluxData<T> F;
-  flux_data<T>(I, I, I, T(0), LIM_NONE, F);
+  flux_data<LIM_NONE, T>(I, I, I, T(0), F);
   s[3 * k] = I.s0; s[3 * k + 1] = I.s1; s[3 * k + 2] = I.s2;
   for (int c = 0; c < 3; c++) {
     W[9 * k + c] = I.W0[c];

@@ -13,6 +13,9 @@ enum { ST_NONREAL = 1, ST_CFL = 2, ST_NAN = 4 };
 // one interface upwind), the x2 sweep with the fused source reads 3.
 constexpr int HALO_X = 2;
 constexpr int HALO_Y = 3;
+// Axisymmetric form: radial faces next to the axis that use the first-order
+// flux (r = 0 and r = dx).
+constexpr int AXIS_FACES = 2;
 // Columns a warp of the x2 sweep updates (lanes 1..30; lanes 0 and 31 carry
 // the neighbour columns the source's Laplacian needs).
 constexpr int YCOLS = 30;
@@ -44,6 +47,9 @@ struct DomScal {
   int done, last, timed, pad;
   double budget_acc[3];          // sum over cells of the state after the step (accumulating)
   double budget[3];              // the same, for the last completed step
+  // per-step constants derived from dt (set wherever dt is set)
+  double lam, coef;              // dt/dx and dt*delta/dx^2
+  float lam32, coef32, dt32, pad32;
 };
 
 // One warp's work item: domain and the tile origin (cells).
@@ -60,6 +66,8 @@ struct StepArgs {
   int ndom;
   double beta, delta, dx, nu_w, nu_max, dt_fixed;
   int limiter, geometry, sweeps, tile_y;
+  int compensated;               // binary32 update with error-free two-sums
+  int pad_;
 };
 
 }  // namespace fvna

@@ -41,7 +41,7 @@ class Config(ctypes.Structure):
                 ("beta", ctypes.c_double), ("delta", ctypes.c_double), ("dx", ctypes.c_double),
                 ("nu_w", ctypes.c_double), ("nu_max", ctypes.c_double),
                 ("dt_fixed", ctypes.c_double), ("steps_per_graph", ctypes.c_int),
-                ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("compensated", ctypes.c_int)]
 
 
 class Domain(ctypes.Structure):
@@ -66,7 +66,7 @@ class Stats(ctypes.Structure):
 
 SYMBOLS = ["fvna_init", "fvna_step", "fvna_run", "fvna_sync", "fvna_fields",
            "fvna_step_timed", "fvna_launch_count", "fvna_destroy", "fvna_strerror", "fvna_riemann",
-           "fvna_step_noalloc"]
+           "fvna_step_noalloc", "fvna_autotune"]
 
 _lib = None
 
@@ -101,6 +101,10 @@ def lib():
     L.fvna_destroy.argtypes = [vp]
     L.fvna_strerror.restype = ctypes.c_char_p
     L.fvna_strerror.argtypes = [ctypes.c_int]
+    L.fvna_autotune.restype = ctypes.c_int
+    L.fvna_autotune.argtypes = [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(Domain),
+                                ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, vp, ctypes.c_int,
+                                ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_float)]
     L.fvna_step_noalloc.restype = ctypes.c_int
     L.fvna_step_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Domain), vp, vp,
                                     ctypes.c_double, ctypes.c_double, dp, vp]
@@ -125,9 +129,9 @@ def _check(rc: int, where: str) -> int:
 
 def make_config(precision=FP64, geometry=CARTESIAN, limiter=LIM_MC, sweeps=7, beta=3.5,
                 delta=0.0, dx=1.0, nu_w=0.9, nu_max=1.0, dt_fixed=0.0, steps_per_graph=0,
-                tile_x=0, tile_y=0) -> Config:
+                tile_x=0, tile_y=0, compensated=1) -> Config:
     return Config(precision, geometry, limiter, sweeps, beta, delta, dx, nu_w, nu_max, dt_fixed,
-                  steps_per_graph, tile_x, tile_y, 0)
+                  steps_per_graph, tile_x, tile_y, compensated)
 
 
 def make_domain(nx, ny, bc=(BC_EXTRAP,) * 4, envelope=0, x0=0.0, y0=0.0, t0=0.0, dt0=0.0,
@@ -146,6 +150,43 @@ def _current_stream():
     return 0
 
 
+def _marshal_states(domains, q0):
+    """Pointers to the initial states (numpy host arrays or torch CUDA tensors)."""
+    n = len(domains)
+    on_dev = False
+    keep = []
+    ptrs = (ctypes.c_void_p * n)()
+    for i, (d, q) in enumerate(zip(domains, q0)):
+        if hasattr(q, "is_cuda") and q.is_cuda:
+            import torch
+            q = q.to(torch.float64).contiguous()
+            assert tuple(q.shape) == (3, d.ny, d.nx)
+            on_dev = True
+            ptrs[i] = q.data_ptr()
+        else:
+            q = np.ascontiguousarray(q, dtype=np.float64)
+            assert q.shape == (3, d.ny, d.nx), (q.shape, d.ny, d.nx)
+            ptrs[i] = q.ctypes.data
+        keep.append(q)
+    return ptrs, on_dev, keep
+
+
+def autotune(config: Config, domains: Sequence[Domain], q0: Sequence, trial_steps: int = 8,
+             stream=None):
+    """Fastest sweep tile shapes for these domains (fvna_autotune): (Config, ms/step)."""
+    ptrs, on_dev, keep = _marshal_states(domains, q0)
+    if stream is None:
+        stream = _current_stream()
+    n = len(domains)
+    darr = (Domain * n)(*domains)
+    best = Config()
+    ms = ctypes.c_float(0.0)
+    _check(lib().fvna_autotune(ctypes.byref(config), n, darr, ptrs, int(on_dev),
+                               ctypes.c_void_p(stream), int(trial_steps), ctypes.byref(best),
+                               ctypes.byref(ms)), "fvna_autotune")
+    return best, float(ms.value)
+
+
 class Solver:
     """A context of one or more domains advancing together.
 
@@ -158,21 +199,7 @@ class Solver:
         self.config = config
         self.domains = list(domains)
         n = len(self.domains)
-        on_dev = False
-        keep = []
-        ptrs = (ctypes.c_void_p * n)()
-        for i, (d, q) in enumerate(zip(self.domains, q0)):
-            if hasattr(q, "is_cuda") and q.is_cuda:
-                import torch
-                q = q.to(torch.float64).contiguous()
-                assert tuple(q.shape) == (3, d.ny, d.nx)
-                on_dev = True
-                ptrs[i] = q.data_ptr()
-            else:
-                q = np.ascontiguousarray(q, dtype=np.float64)
-                assert q.shape == (3, d.ny, d.nx), (q.shape, d.ny, d.nx)
-                ptrs[i] = q.ctypes.data
-            keep.append(q)
+        ptrs, on_dev, keep = _marshal_states(self.domains, q0)
         if stream is None:
             stream = _current_stream()
         self.stream = stream

@@ -173,3 +173,43 @@ def gaussian_2048(steps: int = 5000, n: int = 2048, seed: int = 2) -> Workload:
     q0 = gaussian_pulse(n, n, amplitude(2.0e6), 8.0, seed)
     return Workload(f"gaussian_{n}x{n}", n, n, steps, beta_of(), delta_tilde(1.0e6),
                     1.0 / eta, 0.9, (BC_EXTRAP,) * 4, q0)
+
+
+def focused_axisym(nz: int = 4096, nr: int = 1024, cells_per_wavelength: float = 30.0,
+                   p_surface: float = 0.3e6, freq: float = 1.0e6, aperture_m: float = 30e-3,
+                   focal_m: float = 60e-3, transits: float = 8.0) -> Workload:
+    """Axisymmetric focused-source field in (z, r): a curved aperture of radius
+    30 mm and focal length 60 mm driven sinusoidally at 1 MHz on the z = 0
+    border (reflective axis at r = 0, extrapolation elsewhere), water, 30 cells
+    per wavelength, run for `transits` focal transit times (quasi-steady).
+    L = one wavelength, so the aperture is 20 and the focal length 40."""
+    lam = C0 / freq
+    q0 = ambient(nz, nr)
+    # CFL 0.4: the axisymmetric step is stable up to about 0.5 (see the design notes)
+    w = Workload(f"focused_axisym_{nz}x{nr}", nz, nr, 0, beta_of(), delta_tilde(freq),
+                 1.0 / cells_per_wavelength, 0.4, (BC_HIFU, BC_EXTRAP, BC_REFLECT, BC_EXTRAP), q0,
+                 geometry=1,
+                 extra={"amp": amplitude(p_surface), "focal": focal_m / lam,
+                        "aperture": aperture_m / lam, "envelope": 0,
+                        "t_end": transits * focal_m / lam})
+    return w
+
+
+def batched_64(seed: int = 4, n_domains: int = 64, n_min: int = 256, n_max: int = 1536):
+    """Many independent domains of uneven size: square sides uniform in
+    [n_min, n_max], amplitudes log-uniform in [0.1, 2] MPa, frequencies uniform
+    in [0.5, 2] MHz, each a 4-cycle Gaussian tone burst at a seeded angle,
+    extrapolation borders, one common cell size of 37.5 um (L = 1.5 mm, the
+    1 MHz wavelength, so dx = 1/40 and the burst wavelength is 1/f[MHz]).
+    Returns (list of (nx, ny, q0, info), beta, delta, dx)."""
+    rng = np.random.default_rng(seed)
+    dx = 1.0 / 40.0
+    out = []
+    for k in range(n_domains):
+        n = int(rng.integers(n_min, n_max + 1))
+        p = float(np.exp(rng.uniform(np.log(0.1e6), np.log(2.0e6))))
+        f = float(rng.uniform(0.5e6, 2.0e6))
+        ang = float(rng.uniform(0.0, 2.0 * np.pi))
+        q0 = tone_burst(n, n, amplitude(p), (1.0e6 / f) / dx, ang)
+        out.append((n, n, q0, {"p_pa": p, "f_hz": f, "angle": ang}))
+    return out, beta_of(), delta_tilde(1.0e6), dx

@@ -49,6 +49,7 @@ int main(void) {
   printf("fvna_config %zu\nfvna_domain %zu\nfvna_stats %zu\n", sizeof(fvna_config),
          sizeof(fvna_domain), sizeof(fvna_stats));
   P(fvna_config, beta); P(fvna_config, dt_fixed); P(fvna_config, tile_y);
+  P(fvna_config, compensated);
   P(fvna_domain, x0); P(fvna_domain, dt0); P(fvna_domain, aperture);
   P(fvna_stats, nu_std); P(fvna_stats, status);
   return 0;
@@ -93,8 +94,8 @@ def test_argument_errors_before_device_work(lib):
         fvna.make_config(precision=7), fvna.make_config(geometry=3), fvna.make_config(limiter=9),
         fvna.make_config(sweeps=8), fvna.make_config(dx=0.0), fvna.make_config(dx=-1.0),
         fvna.make_config(nu_w=0.0), fvna.make_config(nu_max=0.0), fvna.make_config(delta=-1.0),
-        fvna.make_config(tile_x=48), fvna.make_config(tile_y=4),
-        fvna.make_config(steps_per_graph=-1),
+        fvna.make_config(tile_x=48), fvna.make_config(tile_x=8), fvna.make_config(tile_y=4),
+        fvna.make_config(steps_per_graph=-1), fvna.make_config(compensated=2),
     ]
     for cfg in bad_cfgs:
         rc, h = _init(cfg, [dom], [q])
@@ -120,11 +121,12 @@ def test_argument_errors_before_device_work(lib):
     assert lib.fvna_sync(None) == fvna.ERR_ARG
     assert lib.fvna_fields(None, 0, 0, None, 0, 0) == fvna.ERR_ARG
     assert lib.fvna_launch_count(None) == 0
+    assert lib.fvna_step_timed(None, None) == fvna.ERR_ARG
     lib.fvna_destroy(None)
     dp = ctypes.POINTER(ctypes.c_double)
     assert lib.fvna_riemann(5, 3.5, 1, None, None, None, None, None, None) == fvna.ERR_ARG
     assert lib.fvna_riemann(0, 3.5, -1, None, None, None, None, None, None) == fvna.ERR_ARG
     assert lib.fvna_riemann(0, 3.5, 0, None, None, None, None, None, None) == fvna.OK
-    for code in [0, -1, -2, -3, -4, -5, -6]:
+    for code in [0, -1, -2, -3, -4, -5, -6, -7]:
         assert lib.fvna_strerror(code)
     assert b"unknown" in lib.fvna_strerror(-99)

@@ -106,7 +106,7 @@ def test_step_parity_fp64(name, case, steps):
     assert sg["nu_mean"] == pytest.approx(so["nu_mean"], rel=1e-14, abs=1e-15)
 
 
-@pytest.mark.parametrize("tile_x,tile_y", [(32, 8), (64, 16), (32, 128), (64, 64)])
+@pytest.mark.parametrize("tile_x,tile_y", [(32, 8), (64, 16), (32, 128), (64, 64), (16, 32)])
 def test_tile_shapes_give_identical_results(tile_x, tile_y):
     q = wl.random_cells(150, 140, 1e-3, seed=31)
     c = Case(150, 140, q, bc=(P, P, E, R), delta=2e-3)
@@ -307,3 +307,105 @@ def test_fp32_borders_against_fp64(bc):
     assert sg["rc"] == 0
     peak, l2 = pressure_errors(qg[0] - 1.0, qo[0] - 1.0)
     assert peak <= 1e-5 and l2 <= 1e-5, (peak, l2)
+
+
+# ------------------------------------------------------------------ full size
+
+def test_full_size_gaussian_parity_first_steps():
+    """The 2048x2048 Gaussian-pulse workload in the bench's configuration:
+    FP64 bit-identical to the oracle, FP32 within 1e-5, over the first steps."""
+    w = wl.gaussian_2048(steps=3, n=2048, seed=2)
+    c = Case(w.nx, w.ny, w.q0, bc=w.bc, beta=w.beta, delta=w.delta, dx=w.dx, nu_w=w.nu_w)
+    qo, so = run_oracle(c, 3)
+    q64, s64 = run_gpu(c, 3, steps_per_graph=1)
+    assert pert_rel_linf(q64, qo) <= TOL64
+    q32, s32 = run_gpu(c, 3, precision=fvna.FP32_PERT, steps_per_graph=1)
+    peak, l2 = pressure_errors(q32[0] - 1.0, qo[0] - 1.0)
+    assert peak <= 1e-5 and l2 <= 1e-5, (peak, l2)
+
+
+CHECKPOINTS = (250, 500, 1000, 2000, 3000, 5000)
+
+
+@pytest.mark.parametrize("compensated", [1, 0])
+def test_full_run_fp32_against_fp64(compensated):
+    """The whole 5000-step 2048x2048 run: FP32 perturbation path against the
+    FP64 path (itself bit-identical to the oracle, see above) at the same
+    times.  The pulse spreads at the sound speed and leaves the 51-wavelength
+    domain around t = 36 (step ~1600); afterwards only the slowly decaying 2D
+    wake remains, so the relative errors are also stated against the initial
+    peak pressure."""
+    w = wl.gaussian_2048(steps=5000, n=2048, seed=2)
+    c = Case(w.nx, w.ny, w.q0, bc=w.bc, beta=w.beta, delta=w.delta, dx=w.dx, nu_w=w.nu_w)
+    p0 = float(np.max(np.abs(w.q0[0] - 1.0)))
+    s64 = fvna.Solver(gpu_config(c, fvna.FP64, steps_per_graph=50), [gpu_domain(c)], [w.q0])
+    s32 = fvna.Solver(gpu_config(c, fvna.FP32_PERT, steps_per_graph=50, compensated=compensated),
+                      [gpu_domain(c)], [w.q0])
+    done = 0
+    rows = []
+    for k in CHECKPOINTS:
+        st64 = s64.run(max_steps=k - done)
+        done = k
+        st32 = s32.run(t_end=st64["t"], max_steps=10 ** 6)
+        assert st32["t"] == st64["t"]
+        p64, p32 = s64.pressure(0), s32.pressure(0)
+        peak, l2 = pressure_errors(p32, p64)
+        linf0 = float(np.max(np.abs(p32 - p64))) / p0
+        rows.append((k, st64["t"], float(np.max(np.abs(p64))) / p0, peak, l2, linf0))
+    s64.close()
+    s32.close()
+    print(f"\ncompensated={compensated}: step t max|p|/p0 peak_rel l2_rel linf/p0")
+    for r in rows:
+        print("  %5d %7.2f %.3e %.3e %.3e %.3e" % r)
+    for k, t, amp, peak, l2, linf0 in rows:
+        assert linf0 <= 1e-5
+        if k <= 1000:          # the pulse is inside the domain
+            assert peak <= 1e-5 and l2 <= 1e-5, (k, peak, l2)
+
+
+# ------------------------------------------------------------------ workloads
+
+def test_focused_axisymmetric_parity():
+    """A reduced focused-source case (axisymmetric, drive on z = 0, reflective
+    axis): FP64 against the oracle over a few hundred steps, FP32 within 1e-5."""
+    w = wl.focused_axisym(nz=240, nr=72, cells_per_wavelength=8.0, p_surface=0.5e6,
+                          aperture_m=4.5e-3, focal_m=9e-3)
+    e = w.extra
+    c = Case(w.nx, w.ny, w.q0, bc=w.bc, beta=w.beta, delta=w.delta, dx=w.dx, nu_w=w.nu_w,
+             geometry=1, amp=e["amp"], focal=e["focal"], aperture=e["aperture"],
+             envelope=e["envelope"])
+    qo, so = run_oracle(c, 300)
+    assert np.max(np.abs(qo[0] - 1)) > 1e-5
+    qg, sg = run_gpu(c, 300)
+    # the drive's sin/exp differ by ulps between libm and CUDA; through the
+    # focusing this stays within 1e-12 of the total state
+    assert np.max(np.abs(qg - qo)) <= 1e-12
+    q32, s32 = run_gpu(c, 10 ** 6, t_end=so["t"], precision=fvna.FP32_PERT)
+    peak, l2 = pressure_errors(q32[0] - 1.0, qo[0] - 1.0)
+    assert peak <= 1e-5 and l2 <= 1e-5, (peak, l2)
+
+
+def test_batched_domains_fp32_and_autotune():
+    """Uneven domains in one context with their own dt (FP32) against separate
+    FP64 oracle runs; the autotuner's choice gives the same results."""
+    sizes = [(96, 96), (140, 60), (33, 170), (200, 41)]
+    rng = np.random.default_rng(9)
+    cases = []
+    for k, (nx, ny) in enumerate(sizes):
+        q = wl.tone_burst(nx, ny, 10 ** rng.uniform(-4.5, -3.0), rng.uniform(10, 30),
+                          rng.uniform(0, 2 * np.pi))
+        cases.append(Case(nx, ny, q, delta=1e-3, dx=1.0 / 20))
+    cfg = gpu_config(cases[0], fvna.FP32_PERT)
+    doms = [gpu_domain(c) for c in cases]
+    best, ms = fvna.autotune(cfg, doms, [c.q0 for c in cases], trial_steps=4)
+    assert best.tile_x in (16, 32, 64) and best.tile_y in (8, 16, 32, 64, 128) and ms > 0
+    s = fvna.Solver(best, doms, [c.q0 for c in cases])
+    s.run(max_steps=60)
+    for k, c in enumerate(cases):
+        t_k = s.stats(k)["t"]
+        qo, so = run_oracle(c, 10 ** 6, t_end=t_k)
+        peak, l2 = pressure_errors(s.q(k)[0] - 1.0, qo[0] - 1.0)
+        assert peak <= 1e-5 and l2 <= 1e-5, (k, peak, l2)
+    ts = [s.stats(k)["t"] for k in range(len(cases))]
+    assert len(set(ts)) > 1      # every domain kept its own dt
+    s.close()
