@@ -229,6 +229,49 @@ int fvna_riemann(int precision, double beta, int n, const double *qL, const doub
 int fvna_step_noalloc(const fvna_config *cfg, const fvna_domain *dom, const double *q_in,
                       double *q_out, double t, double dt, double *smax_out, void *stream);
 
+/* ---- learned sub-grid correction (not in the paper) ----------------------
+ * A small convolutional network applied to coarse runs: three 3x3
+ * convolutions with zero padding, 3 -> 32 -> 32 -> 3 channels, ReLU after
+ * the first two:  y[o,i,j] = b[o] + sum_c sum_{u,v} w[o,c,u,v] x[c,i+u-1,j+v-1].
+ * Weights and hidden activations are bfloat16, accumulation is FP32 (tensor
+ * cores); training keeps FP32 master weights.  Parameters are one flat FP32
+ * vector: w1 (32x3x3x3), b1 (32), w2 (32x32x3x3), b2 (32), w3 (3x32x3x3),
+ * b3 (3), weights ordered [out][in][row][col].  Network tensors are FP32
+ * channel planes (batch, 3, h, w), device memory; hidden activations are
+ * kept by the network between a forward and the matching backward. */
+#define FVNA_NET_PARAMS 11011
+typedef struct fvna_net fvna_net;
+
+/* fvna_net_create -- allocate a network on the current device from host
+ * parameters (FVNA_NET_PARAMS floats, copied). */
+int fvna_net_create(const float *params, fvna_net **out);
+/* fvna_net_params -- copy the parameters out (dst, host) and/or replace them (src, host). */
+int fvna_net_params(fvna_net *net, float *dst, const float *src);
+/* fvna_net_forward -- y = net(in_scale * x) for a batch; x, y device FP32
+ * planes (batch, 3, h, w).  h1_out / h2_out (device, or NULL) receive the two
+ * hidden activations as bfloat16 bit patterns, pixel-major with 32 channels
+ * (batch, h, w, 32).  Blocks. */
+int fvna_net_forward(fvna_net *net, int batch, int h, int w, const float *x, float in_scale,
+                     float *y, unsigned short *h1_out, unsigned short *h2_out, void *stream);
+/* fvna_net_backward -- gradients of sum(gy * y) w.r.t. the parameters for the
+ * last forward (same x, batch and size); gy device FP32 planes; grads (device,
+ * FVNA_NET_PARAMS floats, or NULL). */
+int fvna_net_backward(fvna_net *net, int batch, int h, int w, const float *x, float in_scale,
+                      const float *gy, float *grads, void *stream);
+/* fvna_net_train_step -- one Adam step (lr, beta 0.9/0.999) on the mean squared
+ * error between net(in_scale * x) and target (device FP32 planes) over the
+ * pixels at least `margin` from the image edges (crops of a larger field:
+ * their edges see zero padding the full field does not); loss (host, or NULL)
+ * receives the loss before the step. */
+int fvna_net_train_step(fvna_net *net, int batch, int h, int w, const float *x, float in_scale,
+                        const float *target, int margin, float lr, double *loss, void *stream);
+/* fvna_net_destroy -- free the network (NULL is a no-op). */
+void fvna_net_destroy(fvna_net *net);
+/* fvna_set_correction -- after every step of a single-domain FVNA_FP32_PERT
+ * context, add out_scale * net(in_scale * (q1-1, q2, q3)) to the state
+ * (net = NULL detaches).  The network is borrowed and must outlive its use. */
+int fvna_set_correction(fvna_ctx *ctx, fvna_net *net, float in_scale, float out_scale);
+
 #ifdef __cplusplus
 }
 #endif

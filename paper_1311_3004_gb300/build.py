@@ -6,6 +6,7 @@ the static CUDA runtime:
   fvna_fp32.cu  binary32 perturbation kernels
   fvna_api.cu   host runtime behind include/fvna.h
   fvna_noalloc.cu  the allocation-free binary64 step (fixed device scratch array)
+  fvna_net.cu   the learned correction (BF16 tensor-core forward, FP32 backward)
 """
 from __future__ import annotations
 
@@ -26,6 +27,7 @@ UNITS = {
     "fvna_fp32": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "fvna_api": [],
     "fvna_noalloc": ["-fmad=false"],
+    "fvna_net": [],
 }
 
 

@@ -18,6 +18,7 @@
 
 #include "../../include/fvna.h"
 #include "fvna_launch.h"
+#include "fvna_net.h"
 
 using namespace fvna;
 
@@ -46,6 +47,10 @@ struct fvna_ctx {
   DomScal *h_scal = nullptr;  // pinned mirror
   long long launches = 0;
   int kernels_per_step = 3;
+  // learned correction applied after every step (single FP32 domain)
+  fvna_net *net = nullptr;
+  float net_in = 1.f, net_out = 1.f;
+  __nv_bfloat16 *net_h = nullptr;   // two hidden activation buffers
 };
 
 namespace {
@@ -115,6 +120,7 @@ void free_ctx(fvna_ctx *c) {
   cudaFree(c->d_ty);
   cudaFree(c->d_state);
   cudaFree(c->d_stage);
+  cudaFree(c->net_h);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete c;
 }
@@ -123,6 +129,14 @@ int enqueue_steps_raw(fvna_ctx *c, cudaStream_t s, int nsteps) {
   for (int i = 0; i < nsteps; i++) {
     CK(launch_sweep_x(c->cfg.precision, c->tile_x, c->args_x, c->blocks_x, s));
     CK(launch_sweep_y(c->cfg.precision, c->args_y, c->blocks_y, s));
+    if (c->net) {
+      const DomDev &d = c->dd[0];
+      size_t pix = (size_t)d.nx * d.ny;
+      long long pstride = (long long)(((char *)d.qa[1] - (char *)d.qa[0]) / sizeof(float));
+      CK(net_forward_launch(c->net, 1, d.ny, d.nx, (const float *)d.qa[0], pstride, d.pitch, 0,
+                            c->net_in, (float *)d.qa[0], pstride, d.pitch, 0, 1, c->net_out,
+                            c->net_h, c->net_h + pix * 32, s, &c->d_scal[0].done));
+    }
     CK(launch_advance(c->args, s));
   }
   return FVNA_OK;
@@ -555,6 +569,23 @@ int fvna_autotune(const fvna_config *cfg, int n, const fvna_domain *doms, const 
   winner.steps_per_graph = cfg->steps_per_graph;
   *best = winner;
   if (ms_per_step) *ms_per_step = best_ms / (float)trial_steps;
+  return FVNA_OK;
+}
+
+int fvna_set_correction(fvna_ctx *c, fvna_net *net, float in_scale, float out_scale) {
+  if (!c) return FVNA_ERR_ARG;
+  if (net && (c->ndom != 1 || c->cfg.precision != FVNA_FP32_PERT)) return FVNA_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  c->net = net;
+  c->net_in = in_scale;
+  c->net_out = out_scale;
+  c->kernels_per_step = net ? 6 : 3;
+  if (net && !c->net_h) {
+    size_t pix = (size_t)c->dd[0].nx * c->dd[0].ny;
+    CK(cudaMalloc(&c->net_h, 2 * pix * 32 * sizeof(__nv_bfloat16)));
+  }
   return FVNA_OK;
 }
 

@@ -66,7 +66,9 @@ class Stats(ctypes.Structure):
 
 SYMBOLS = ["fvna_init", "fvna_step", "fvna_run", "fvna_sync", "fvna_fields",
            "fvna_step_timed", "fvna_launch_count", "fvna_destroy", "fvna_strerror", "fvna_riemann",
-           "fvna_step_noalloc", "fvna_autotune"]
+           "fvna_step_noalloc", "fvna_autotune", "fvna_net_create", "fvna_net_params",
+           "fvna_net_forward", "fvna_net_backward", "fvna_net_train_step", "fvna_net_destroy",
+           "fvna_set_correction"]
 
 _lib = None
 
@@ -105,6 +107,24 @@ def lib():
     L.fvna_autotune.argtypes = [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(Domain),
                                 ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, vp, ctypes.c_int,
                                 ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_float)]
+    L.fvna_net_create.restype = ctypes.c_int
+    L.fvna_net_create.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(vp)]
+    L.fvna_net_params.restype = ctypes.c_int
+    L.fvna_net_params.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+    L.fvna_net_forward.restype = ctypes.c_int
+    L.fvna_net_forward.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
+                                   ctypes.c_float, vp, vp, vp, vp]
+    L.fvna_net_backward.restype = ctypes.c_int
+    L.fvna_net_backward.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
+                                    ctypes.c_float, vp, vp, vp]
+    L.fvna_net_train_step.restype = ctypes.c_int
+    L.fvna_net_train_step.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
+                                      ctypes.c_float, vp, ctypes.c_int, ctypes.c_float,
+                                      ctypes.POINTER(ctypes.c_double), vp]
+    L.fvna_net_destroy.restype = None
+    L.fvna_net_destroy.argtypes = [vp]
+    L.fvna_set_correction.restype = ctypes.c_int
+    L.fvna_set_correction.argtypes = [vp, vp, ctypes.c_float, ctypes.c_float]
     L.fvna_step_noalloc.restype = ctypes.c_int
     L.fvna_step_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Domain), vp, vp,
                                     ctypes.c_double, ctypes.c_double, dp, vp]
@@ -267,6 +287,13 @@ class Solver:
     def launch_count(self) -> int:
         return int(lib().fvna_launch_count(self._h))
 
+    def set_correction(self, net, in_scale: float, out_scale: float) -> None:
+        """Add out_scale * net(in_scale * state) after every step (net=None detaches)."""
+        self._net = net
+        _check(lib().fvna_set_correction(self._h, net._h if net is not None else None,
+                                         float(in_scale), float(out_scale)),
+               "fvna_set_correction")
+
     def close(self):
         if getattr(self, "_h", None):
             lib().fvna_destroy(self._h)
@@ -277,6 +304,102 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+NET_PARAMS = 11011
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Net:
+    """The learned correction network (fvna_net_*): torch CUDA tensors in and
+    out, all arithmetic in the library's kernels."""
+
+    def __init__(self, params: np.ndarray):
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        assert p.size == NET_PARAMS
+        h = ctypes.c_void_p()
+        _check(lib().fvna_net_create(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                     ctypes.byref(h)), "fvna_net_create")
+        self._h = h
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(NET_PARAMS, dtype=np.float32)
+        _check(lib().fvna_net_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                     None), "fvna_net_params")
+        return out
+
+    def set_params(self, params: np.ndarray) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        _check(lib().fvna_net_params(self._h, None,
+                                     p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "fvna_net_params")
+
+    def forward(self, x, in_scale: float = 1.0, hidden: bool = False, stream=None):
+        """x: (B, 3, h, w) float32 CUDA tensor -> y (and the two bf16 hidden
+        activations as int16 bit patterns (B, h, w, 32) if hidden)."""
+        import torch
+        B, C, H, W = x.shape
+        y = torch.empty_like(x)
+        h1 = h2 = None
+        if hidden:
+            h1 = torch.empty((B, H, W, 32), dtype=torch.int16, device=x.device)
+            h2 = torch.empty_like(h1)
+        _check(lib().fvna_net_forward(self._h, B, H, W, _ptr(x), float(in_scale), _ptr(y),
+                                      _ptr(h1), _ptr(h2),
+                                      ctypes.c_void_p(stream or _current_stream())),
+               "fvna_net_forward")
+        return (y, h1, h2) if hidden else y
+
+    def backward(self, x, gy, in_scale: float = 1.0, stream=None):
+        import torch
+        B, C, H, W = x.shape
+        g = torch.empty(NET_PARAMS, dtype=torch.float32, device=x.device)
+        _check(lib().fvna_net_backward(self._h, B, H, W, _ptr(x), float(in_scale), _ptr(gy),
+                                       _ptr(g), ctypes.c_void_p(stream or _current_stream())),
+               "fvna_net_backward")
+        return g
+
+    def train_step(self, x, target, lr: float, in_scale: float = 1.0, margin: int = 0,
+                   stream=None) -> float:
+        B, C, H, W = x.shape
+        loss = ctypes.c_double(0.0)
+        _check(lib().fvna_net_train_step(self._h, B, H, W, _ptr(x), float(in_scale), _ptr(target),
+                                         int(margin), float(lr), ctypes.byref(loss),
+                                         ctypes.c_void_p(stream or _current_stream())),
+               "fvna_net_train_step")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fvna_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def net_params_flat(p: dict) -> np.ndarray:
+    """Flatten a parameter dict (w1 b1 w2 b2 w3 b3, [out][in][row][col]) to the ABI layout."""
+    return np.concatenate([np.asarray(p[k], dtype=np.float32).reshape(-1)
+                           for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+
+
+def net_params_dict(flat: np.ndarray) -> dict:
+    flat = np.asarray(flat, dtype=np.float64)
+    shapes = [("w1", (32, 3, 3, 3)), ("b1", (32,)), ("w2", (32, 32, 3, 3)), ("b2", (32,)),
+              ("w3", (3, 32, 3, 3)), ("b3", (3,))]
+    out, o = {}, 0
+    for k, sh in shapes:
+        n = int(np.prod(sh))
+        out[k] = flat[o:o + n].reshape(sh)
+        o += n
+    return out
 
 
 def step_noalloc(config: Config, domain: Domain, q_in, q_out, t: float, dt: float,
