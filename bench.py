@@ -56,7 +56,8 @@ def parse():
                     help="domain side (the headline is 2048; other sizes are for profiling)")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=["gaussian", "plane", "focused", "batched"],
+    ap.add_argument("--workload", choices=["gaussian", "plane", "focused", "batched", "learned",
+                                           "netfwd"],
                     default="gaussian",
                     help="gaussian: the headline line; the others print their own line")
     ap.add_argument("--no-e2e", action="store_true")
@@ -276,13 +277,10 @@ def run_native(args):
                                               0 if args.plain_update else 1)
     torch.cuda.synchronize()
     step_ms = per.sum(axis=1)
-    total_s = float(step_ms.sum()) / 1e3
+    from paper_1311_3004_gb300.replicas import job_throughput
+    value, total_s, _ = job_throughput(float(step_ms.sum()) / 1e3, float(cells * args.steps))
     if world > 1:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         torch.distributed.barrier()
-        total_s = float(t.item())
-    value = cells * args.steps * world / total_s
 
     # roofline of the dominant kernel (x1 sweep or x2 sweep + source)
     esz = 4 if prec == fvna.FP32_PERT else 8
@@ -499,8 +497,77 @@ def run_batched(args):
     return 0
 
 
+def run_learned(args):
+    """Coarse (2048x512) focused-source runs with the learned correction
+    against the plain fine-grid (4096x1024) FP64 solver: training data from
+    fine/coarse solver pairs at five surface pressures, training on the GPU,
+    evaluation on a pressure not trained on; focal peak error and
+    time-to-solution."""
+    torch, fvna = _setup_cuda()
+    from paper_1311_3004_gb300 import learned
+    spec = learned.FULL
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    (X, T), gen_s = _timed(torch, lambda: learned.generate(spec, [0.1e6, 0.2e6, 0.3e6, 0.4e6,
+                                                                   0.5e6], log=log))
+    (net, info), train_s = _timed(torch, lambda: learned.train_net(X, T, steps=4000, crop=128,
+                                                                  batch=8, lr=5e-4, noise=0.05,
+                                                                  importance=True, log=log))
+    res = learned.evaluate(spec, 0.35e6, net, info, gains=(1.0, 0.5))
+    net.close()
+    cells_c = spec.nz * spec.nr
+    c, cn = res["coarse"], res["coarse_net"]
+    line = {"metric": METRIC, "unit": METRIC, "workload": "learned_focused_axisym_2048x512",
+            "dtype": "f32+bf16", "value": cells_c * (spec.t_end / spec.dt(False)) / cn["seconds"],
+            "time_to_solution_s": cn["seconds"],
+            "fine_fp64_time_to_solution_s": res["fine_seconds"],
+            "speedup_vs_fine_fp64": res["fine_seconds"] / cn["seconds"],
+            "focal_peak_rel_err": cn["focal_peak_rel_err"], "l2_rel_err": cn["l2_rel_err"],
+            "status": cn.get("status", 0),
+            "gain_0.5": res.get("coarse_net_gain0.5"),
+            "coarse_without_net": {"focal_peak_rel_err": c["focal_peak_rel_err"],
+                                   "l2_rel_err": c["l2_rel_err"], "seconds": c["seconds"]},
+            "train": {"samples": int(X.shape[0]), "data_s": gen_s, "train_s": train_s,
+                      "loss_first": info["loss_first"], "loss_last": info["loss_last"]},
+            "eval_p_surface_pa": 0.35e6, "t_end": res["t_end"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_netfwd(args):
+    """Inference throughput of the correction network (three BF16 tensor-core
+    convolutions) on one 2048x512 coarse field, CUDA-event timed."""
+    torch, fvna = _setup_cuda()
+    from paper_1311_3004_gb300 import learned
+    H, W = 512, 2048
+    net = fvna.Net(learned._init_params(0))
+    x = torch.randn((1, 3, H, W), dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        net.forward(x)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(args.steps):
+        net.forward(x)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    flops = 2.0 * 9 * (3 * 32 + 32 * 32 + 32 * 3) * H * W    # algorithmic multiply-adds x 2
+    pk, kind = peaks()
+    print(json.dumps({"metric": "TFLOP/s", "workload": "net_forward_2048x512", "dtype": "bf16",
+                      "ms_per_forward": ms, "value": flops / (ms * 1e-3) / 1e12,
+                      "roofline": {"bound": "tensor", "peak": pk["bf16_tflops"],
+                                   "frac": flops / (ms * 1e-3) / 1e12 / pk["bf16_tflops"],
+                                   "peak_source": kind},
+                      "note": "includes the host-synchronising wrapper per forward"}), flush=True)
+    net.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "netfwd":
+        return run_netfwd(args)
+    if args.workload == "learned":
+        return run_learned(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "plane":

@@ -261,16 +261,23 @@ int fvna_net_backward(fvna_net *net, int batch, int h, int w, const float *x, fl
 /* fvna_net_train_step -- one Adam step (lr, beta 0.9/0.999) on the mean squared
  * error between net(in_scale * x) and target (device FP32 planes) over the
  * pixels at least `margin` from the image edges (crops of a larger field:
- * their edges see zero padding the full field does not); loss (host, or NULL)
- * receives the loss before the step. */
+ * their edges see zero padding the full field does not).  edges (device,
+ * batch x 4 ints: top, bottom, left, right, or NULL) gives per-image margins
+ * instead, 0 on the sides where a crop meets the field's own edge.  loss
+ * (host, or NULL) receives the loss before the step. */
 int fvna_net_train_step(fvna_net *net, int batch, int h, int w, const float *x, float in_scale,
-                        const float *target, int margin, float lr, double *loss, void *stream);
+                        const float *target, int margin, const int *edges, float lr, double *loss,
+                        void *stream);
 /* fvna_net_destroy -- free the network (NULL is a no-op). */
 void fvna_net_destroy(fvna_net *net);
-/* fvna_set_correction -- after every step of a single-domain FVNA_FP32_PERT
- * context, add out_scale * net(in_scale * (q1-1, q2, q3)) to the state
- * (net = NULL detaches).  The network is borrowed and must outlive its use. */
-int fvna_set_correction(fvna_ctx *ctx, fvna_net *net, float in_scale, float out_scale);
+/* fvna_set_correction -- after every `every`-th step (counted since init) of a
+ * single-domain FVNA_FP32_PERT context, add out_scale * net(in_scale *
+ * (q1-1, q2, q3)) to the state, except on the cells within edge_band cells of
+ * a domain edge (a network trained on crops with a loss margin has not learnt
+ * them); net = NULL detaches.  The network is borrowed and must outlive its
+ * use. */
+int fvna_set_correction(fvna_ctx *ctx, fvna_net *net, float in_scale, float out_scale,
+                        int every, int edge_band);
 
 #ifdef __cplusplus
 }

@@ -50,6 +50,8 @@ struct fvna_ctx {
   // learned correction applied after every step (single FP32 domain)
   fvna_net *net = nullptr;
   float net_in = 1.f, net_out = 1.f;
+  int net_every = 1;
+  int net_band = 0;
   __nv_bfloat16 *net_h = nullptr;   // two hidden activation buffers
 };
 
@@ -125,8 +127,16 @@ void free_ctx(fvna_ctx *c) {
   delete c;
 }
 
+int enqueue_drives(fvna_ctx *c, cudaStream_t s) {
+  for (int d = 0; d < c->ndom; d++)
+    if (c->dd[d].drive) CK(launch_drive(c->cfg.precision, c->args, d, c->dd[d].ny, 0, s));
+  return FVNA_OK;
+}
+
 int enqueue_steps_raw(fvna_ctx *c, cudaStream_t s, int nsteps) {
   for (int i = 0; i < nsteps; i++) {
+    int rc = enqueue_drives(c, s);
+    if (rc != FVNA_OK) return rc;
     CK(launch_sweep_x(c->cfg.precision, c->tile_x, c->args_x, c->blocks_x, s));
     CK(launch_sweep_y(c->cfg.precision, c->args_y, c->blocks_y, s));
     if (c->net) {
@@ -135,7 +145,8 @@ int enqueue_steps_raw(fvna_ctx *c, cudaStream_t s, int nsteps) {
       long long pstride = (long long)(((char *)d.qa[1] - (char *)d.qa[0]) / sizeof(float));
       CK(net_forward_launch(c->net, 1, d.ny, d.nx, (const float *)d.qa[0], pstride, d.pitch, 0,
                             c->net_in, (float *)d.qa[0], pstride, d.pitch, 0, 1, c->net_out,
-                            c->net_h, c->net_h + pix * 32, s, &c->d_scal[0].done));
+                            c->net_h, c->net_h + pix * 32, s, &c->d_scal[0].done,
+                            &c->d_scal[0].step, c->net_every, c->net_band));
     }
     CK(launch_advance(c->args, s));
   }
@@ -221,6 +232,10 @@ cudaError_t launch_sweep_y(int p, const StepArgs &a, int b, cudaStream_t s) {
 cudaError_t launch_speeds(int p, const StepArgs &a, int dom, cudaStream_t s) {
   return p == FVNA_FP64 ? launch_speeds_fp64(a, dom, s) : launch_speeds_fp32(a, dom, s);
 }
+cudaError_t launch_drive(int p, const StepArgs &a, int dom, int ny, int always, cudaStream_t s) {
+  return p == FVNA_FP64 ? launch_drive_fp64(a, dom, ny, always, s)
+                        : launch_drive_fp32(a, dom, ny, always, s);
+}
 cudaError_t launch_import(int p, const DomDev &d, const double *q0, cudaStream_t s) {
   return p == FVNA_FP64 ? launch_import_fp64(d, q0, s) : launch_import_fp32(d, q0, s);
 }
@@ -265,15 +280,19 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   c->tile_x = cfg->tile_x ? cfg->tile_x : 32;
   c->tile_y = cfg->tile_y ? cfg->tile_y : 64;
   c->kernels_per_step = 3;
+  for (int d = 0; d < n; d++) c->kernels_per_step += doms[d].bc[0] == BC_HIFU ? 1 : 0;
 
-  // state planes: 2 sets x 3 planes per domain, each plane 256-byte aligned
-  std::vector<size_t> offs(n);
+  // state planes: 2 sets x 3 planes per domain, each plane 256-byte aligned,
+  // then the HIFU border buffer of domains driven on the x1-low border
+  std::vector<size_t> offs(n), doffs(n);
   size_t total = 0, max_cells = 0;
   for (int d = 0; d < n; d++) {
     size_t pitch = ((size_t)doms[d].nx + 31) / 32 * 32;
     size_t plane = (pitch * doms[d].ny * esz + 255) / 256 * 256;
     offs[d] = total;
     total += 6 * plane;
+    doffs[d] = total;
+    if (doms[d].bc[0] == BC_HIFU) total += (3 * HALO_Y * (size_t)doms[d].ny * esz + 255) / 256 * 256;
     max_cells = std::max(max_cells, (size_t)doms[d].nx * doms[d].ny);
   }
   CK(cudaMalloc(&c->d_state, total));
@@ -298,6 +317,7 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
       g.qa[k] = base + k * plane;
       g.qb[k] = base + (3 + k) * plane;
     }
+    g.drive = D.bc[0] == BC_HIFU ? (char *)c->d_state + doffs[d] : nullptr;
   }
   CK(cudaMemsetAsync(c->d_state, 0, total, c->stream));
   CK(cudaMalloc(&c->d_dd, sizeof(DomDev) * n));
@@ -369,6 +389,10 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
       src = c->d_stage;
     }
     CK(launch_import(prec, c->dd[d], src, c->stream));
+  }
+  // the speed pass reads the border values of the initial time
+  for (int d = 0; d < n; d++) {
+    if (c->dd[d].drive) CK(launch_drive(prec, a, d, doms[d].ny, 1, c->stream));
     // speeds of the initial state -> first dt
     StepArgs sa = a;
     CK(launch_speeds(prec, sa, d, c->stream));
@@ -499,6 +523,7 @@ int fvna_step_timed(fvna_ctx *c, float ms[3]) {
   }
   cudaError_t e = launch_prepare(c->args, -1e300, 1, c->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->stream);
+  if (e == cudaSuccess && enqueue_drives(c, c->stream) != FVNA_OK) e = cudaErrorUnknown;
   if (e == cudaSuccess)
     e = launch_sweep_x(c->cfg.precision, c->tile_x, c->args_x, c->blocks_x, c->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
@@ -572,16 +597,19 @@ int fvna_autotune(const fvna_config *cfg, int n, const fvna_domain *doms, const 
   return FVNA_OK;
 }
 
-int fvna_set_correction(fvna_ctx *c, fvna_net *net, float in_scale, float out_scale) {
-  if (!c) return FVNA_ERR_ARG;
+int fvna_set_correction(fvna_ctx *c, fvna_net *net, float in_scale, float out_scale, int every,
+                        int edge_band) {
+  if (!c || every < 1 || edge_band < 0) return FVNA_ERR_ARG;
   if (net && (c->ndom != 1 || c->cfg.precision != FVNA_FP32_PERT)) return FVNA_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));
   if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
   if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  c->kernels_per_step += (net ? 3 : 0) - (c->net ? 3 : 0);
   c->net = net;
   c->net_in = in_scale;
   c->net_out = out_scale;
-  c->kernels_per_step = net ? 6 : 3;
+  c->net_every = every;
+  c->net_band = edge_band;
   if (net && !c->net_h) {
     size_t pix = (size_t)c->dd[0].nx * c->dd[0].ny;
     CK(cudaMalloc(&c->net_h, 2 * pix * 32 * sizeof(__nv_bfloat16)));

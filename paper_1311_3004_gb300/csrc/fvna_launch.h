@@ -24,6 +24,10 @@ cudaError_t launch_sweep_y(int precision, const StepArgs &a, int blocks, cudaStr
 cudaError_t launch_advance(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_prepare(const StepArgs &a, double t_end, long long max_steps, cudaStream_t s);
 cudaError_t launch_speeds(int precision, const StepArgs &a, int dom, cudaStream_t s);
+cudaError_t launch_drive(int precision, const StepArgs &a, int dom, int ny, int always,
+                         cudaStream_t s);
+cudaError_t launch_drive_fp64(const StepArgs &a, int dom, int ny, int always, cudaStream_t s);
+cudaError_t launch_drive_fp32(const StepArgs &a, int dom, int ny, int always, cudaStream_t s);
 cudaError_t launch_first_dt(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_import(int precision, const DomDev &d, const double *q0, cudaStream_t s);
 cudaError_t launch_export(int precision, const DomDev &d, double *out, int what, cudaStream_t s);

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256) k_net_conv(NetConvArgs a) {
   __shared__ __align__(16) __nv_bfloat16 s_in[NET_HALO_H * NET_HALO_W * CPAD];  // also im2col
   __shared__ __align__(16) __nv_bfloat16 s_w[WROWS * WSTRIDE];
   if (a.done && *a.done) return;   // the step of this domain was not taken
+  if (a.step && a.every > 1 && (*a.step + 1) % a.every != 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int b = blockIdx.z;
   const int i0 = blockIdx.y * NET_TH, j0 = blockIdx.x * NET_TW;
@@ -190,6 +191,8 @@ __global__ void __launch_bounds__(256) k_net_conv(NetConvArgs a) {
           __nv_bfloat162 v = __floats2bfloat162_rn(y0, y1);
           *reinterpret_cast<__nv_bfloat162 *>(a.hout + (((size_t)b * H + gi) * W + gj) * CH + ch) = v;
         } else {
+          if (a.apply && (gj < a.band || gj >= W - a.band || gi < a.band || gi >= H - a.band))
+            continue;
           size_t off = (size_t)b * a.out_bstride + (size_t)gi * a.out_pitch + gj;
           if (ch < 3) {
             float *o = a.out + off + (size_t)ch * a.out_pstride;
@@ -236,15 +239,30 @@ __global__ void k_net_pack(const float *params, __nv_bfloat16 *w1, __nv_bfloat16
 // ---------------------------------------------------------------------------
 // loss = mean over the pixels at least `margin` from the image edge of
 // (y - t)^2, g = 2 (y - t) / N there and 0 elsewhere
+// edges (device, batch x 4: top, bottom, left, right margins) overrides the
+// uniform margin per image side: 0 where a crop side is an edge of the field.
+__global__ void k_net_count(int B, int H, int W, int margin, const int *edges, long long *nin) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  long long s = 0;
+  for (int b = 0; b < B; b++) {
+    int t = edges ? edges[4 * b] : margin, bo = edges ? edges[4 * b + 1] : margin;
+    int l = edges ? edges[4 * b + 2] : margin, r = edges ? edges[4 * b + 3] : margin;
+    s += (long long)(H - t - bo) * (W - l - r);
+  }
+  *nin = s;
+}
+
 __global__ void k_net_mse(const float *y, const float *t, float *g, long long n, int H, int W,
-                          int margin, double *loss) {
-  const long long hi = H - 2 * margin, wi = W - 2 * margin;
-  const long long nin = n / ((long long)H * W) * hi * wi;
+                          int margin, const int *edges, const long long *nin_p, double *loss) {
+  const long long nin = *nin_p;
   double s = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
     int j = (int)(e % W), i = (int)((e / W) % H);
-    bool in = i >= margin && i < H - margin && j >= margin && j < W - margin;
+    int b = (int)(e / (3LL * H * W));
+    int mt = edges ? edges[4 * b] : margin, mb = edges ? edges[4 * b + 1] : margin;
+    int ml = edges ? edges[4 * b + 2] : margin, mr = edges ? edges[4 * b + 3] : margin;
+    bool in = i >= mt && i < H - mb && j >= ml && j < W - mr;
     float d = in ? y[e] - t[e] : 0.f;
     g[e] = 2.f * d / (float)nin;
     s += (double)d * d;
@@ -364,6 +382,7 @@ struct fvna_net {
   __nv_bfloat16 *h1 = nullptr, *h2 = nullptr;                           // activations
   float *y = nullptr, *g3 = nullptr, *gh2 = nullptr, *gh1 = nullptr;
   double *loss = nullptr;
+  long long *nin = nullptr;
   long long cap_pix = 0;  // capacity of the activation buffers (B*H*W)
   int adam_t = 0;
 };
@@ -417,7 +436,8 @@ cudaError_t net_forward_launch(const fvna_net *n, int B, int H, int W, const flo
                                float in_scale, float *out, long long out_pstride, int out_pitch,
                                long long out_bstride, int apply, float out_scale,
                                __nv_bfloat16 *h1, __nv_bfloat16 *h2, cudaStream_t s,
-                               const int *done) {
+                               const int *done, const long long *step, int every,
+                               int band) {
   dim3 grid((W + NET_TW - 1) / NET_TW, (H + NET_TH - 1) / NET_TH, B);
   NetConvArgs a;
   std::memset(&a, 0, sizeof a);
@@ -425,6 +445,9 @@ cudaError_t net_forward_launch(const fvna_net *n, int B, int H, int W, const flo
   a.in = in; a.in_pstride = in_pstride; a.in_pitch = in_pitch; a.in_bstride = in_bstride;
   a.in_scale = in_scale;
   a.done = done;
+  a.step = step;
+  a.every = every;
+  a.band = band;
   a.wmat = n->w1; a.bias = n->params + NET_OFF_B1; a.hout = h1;
   k_net_conv<0><<<grid, 256, 0, s>>>(a);
   a.hin = h1; a.wmat = n->w2; a.bias = n->params + NET_OFF_B2; a.hout = h2;
@@ -457,6 +480,7 @@ int fvna_net_create(const float *params, fvna_net **out) {
     n->w3 = n->w2 + 32 * KH;
     e = cudaMalloc(&n->loss, sizeof(double));
   }
+  if (e == cudaSuccess) e = cudaMalloc(&n->nin, sizeof(long long));
   if (e == cudaSuccess)
     e = cudaMemcpy(n->params, params, FVNA_NET_PARAMS * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(n->m, 0, 2 * FVNA_NET_PARAMS * sizeof(float));
@@ -477,6 +501,7 @@ void fvna_net_destroy(fvna_net *n) {
   cudaFree(n->params);
   cudaFree(n->w1);
   cudaFree(n->loss);
+  cudaFree(n->nin);
   delete n;
 }
 
@@ -530,7 +555,8 @@ int fvna_net_backward(fvna_net *n, int B, int H, int W, const float *x, float in
 }
 
 int fvna_net_train_step(fvna_net *n, int B, int H, int W, const float *x, float in_scale,
-                        const float *target, int margin, float lr, double *loss, void *stream) {
+                        const float *target, int margin, const int *edges, float lr, double *loss,
+                        void *stream) {
   if (!n || !x || !target || B < 1 || H < 1 || W < 1 || !(lr > 0.f)) return FVNA_ERR_ARG;
   if (margin < 0 || 2 * margin >= H || 2 * margin >= W) return FVNA_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -541,8 +567,9 @@ int fvna_net_train_step(fvna_net *n, int B, int H, int W, const float *x, float 
                          n->h1, n->h2, s));
   NCK(cudaMemsetAsync(n->loss, 0, sizeof(double), s));
   long long ny = 3LL * B * hw;
+  k_net_count<<<1, 32, 0, s>>>(B, H, W, margin, edges, n->nin);
   k_net_mse<<<(int)((ny + 255) / 256 < 2048 ? (ny + 255) / 256 : 2048), 256, 0, s>>>(
-      n->y, target, n->g3, ny, H, W, margin, n->loss);
+      n->y, target, n->g3, ny, H, W, margin, edges, n->nin, n->loss);
   NCK(cudaGetLastError());
   rc = fvna_net_backward(n, B, H, W, x, in_scale, n->g3, nullptr, stream);
   if (rc != FVNA_OK) return rc;

@@ -34,6 +34,9 @@ struct NetConvArgs {
   int apply;                       // 1: out += out_scale * y
   float out_scale;
   const int *done;                 // if not NULL and *done != 0: do nothing
+  const long long *step;           // if not NULL: apply only when (*step + 1) % every == 0
+  int every;
+  int band;                        // apply: leave cells within `band` of any edge unchanged
 };
 
 cudaError_t net_forward_launch(const fvna_net *n, int B, int H, int W, const float *in,
@@ -41,6 +44,7 @@ cudaError_t net_forward_launch(const fvna_net *n, int B, int H, int W, const flo
                                float in_scale, float *out, long long out_pstride, int out_pitch,
                                long long out_bstride, int apply, float out_scale,
                                __nv_bfloat16 *h1, __nv_bfloat16 *h2, cudaStream_t s,
-                               const int *done = nullptr);
+                               const int *done = nullptr, const long long *step = nullptr,
+                               int every = 1, int band = 0);
 
 }  // namespace fvna

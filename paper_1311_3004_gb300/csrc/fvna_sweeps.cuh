@@ -71,6 +71,12 @@ __device__ __forceinline__ void load_mapped(const DomDev &D, const typename P::T
     double xc = D.x0 + (gx + 0.5) * dx;
     double yc = D.y0 + (gy + 0.5) * dx;
     if (bc == BC_TAYLOR || (bc == BC_HIFU && side == 0 && yc >= 0.0 && yc <= D.aperture)) {
+      if (bc == BC_HIFU && D.drive && gy >= 0 && gy < ny) {   // evaluated once per step
+        const T *dv = (const T *)D.drive;
+        size_t o = (size_t)(-1 - gx) * ny + gy, ps = (size_t)HALO_Y * ny;
+        out[0] = dv[o]; out[1] = dv[ps + o]; out[2] = dv[2 * ps + o];
+        return;
+      }
       double v[3];
       if (bc == BC_TAYLOR) P::taylor(D, xc, yc, t, v); else P::hifu(D, xc, yc, t, v);
       out[0] = (T)v[0]; out[1] = (T)v[1]; out[2] = (T)v[2];
@@ -433,6 +439,12 @@ template <class P> struct YSink {
     z3 = q2 * r;
   }
   __device__ __forceinline__ void analytic(int bc, int cx, int gy, T o[3]) const {
+    if (bc == BC_HIFU && D->drive && cx < 0 && gy >= 0 && gy < D->ny) {
+      const T *dv = (const T *)D->drive;
+      size_t of = (size_t)(-1 - cx) * D->ny + gy, ps = (size_t)HALO_Y * D->ny;
+      o[0] = dv[of]; o[1] = dv[ps + of]; o[2] = dv[2 * ps + of];
+      return;
+    }
     double v[3];
     double xc = D->x0 + (cx + 0.5) * dx, yc = D->y0 + (gy + 0.5) * dx;
     if (bc == BC_TAYLOR) P::taylor(*D, xc, yc, t, v); else P::hifu(*D, xc, yc, t, v);
@@ -602,6 +614,31 @@ __global__ void __launch_bounds__(128, FVNA_Y_MINBLOCKS) k_sweep_y(StepArgs A) {
       atomicAdd(&S->budget_acc[1], b1);
       atomicAdd(&S->budget_acc[2], b2);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// HIFU drive of the current step (eq. hifuBC) at the ghost columns -1..-3 of
+// every row inside the aperture, evaluated once per step instead of in every
+// load (the drive costs sin/exp in binary64 per value).
+// ---------------------------------------------------------------------------
+template <class P>
+__global__ void k_drive(StepArgs A, int dom, int always) {
+  typedef typename P::T T;
+  const DomDev &D = A.doms[dom];
+  const DomScal *S = A.scal + dom;
+  if ((S->done && !always) || !D.drive) return;
+  const int n = HALO_Y * D.ny;
+  T *dv = (T *)D.drive;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    int layer = e / D.ny, row = e - layer * D.ny;
+    int gx = -1 - layer;
+    double xc = D.x0 + (gx + 0.5) * A.dx, yc = D.y0 + (row + 0.5) * A.dx;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (yc >= 0.0 && yc <= D.aperture) P::hifu(D, xc, yc, S->t, v);
+    dv[e] = (T)v[0];
+    dv[n + e] = (T)v[1];
+    dv[2 * n + e] = (T)v[2];
   }
 }
 

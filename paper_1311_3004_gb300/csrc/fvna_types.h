@@ -32,6 +32,8 @@ struct DomDev {
   double dt0;                   // > 0: first dt given by the caller
   void *qa[3];                  // state planes (start and end of every step)
   void *qb[3];                  // planes after the x1 sweep
+  void *drive;                  // HIFU border values of the current step, 3 planes of
+                                // HALO_Y x ny (ghost column -1-k at k*ny + row), or NULL
 };
 
 // Per-domain scalars that evolve on the device (one step = K1, K2, K3).

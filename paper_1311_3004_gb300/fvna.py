@@ -119,12 +119,13 @@ def lib():
                                     ctypes.c_float, vp, vp, vp]
     L.fvna_net_train_step.restype = ctypes.c_int
     L.fvna_net_train_step.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
-                                      ctypes.c_float, vp, ctypes.c_int, ctypes.c_float,
+                                      ctypes.c_float, vp, ctypes.c_int, vp, ctypes.c_float,
                                       ctypes.POINTER(ctypes.c_double), vp]
     L.fvna_net_destroy.restype = None
     L.fvna_net_destroy.argtypes = [vp]
     L.fvna_set_correction.restype = ctypes.c_int
-    L.fvna_set_correction.argtypes = [vp, vp, ctypes.c_float, ctypes.c_float]
+    L.fvna_set_correction.argtypes = [vp, vp, ctypes.c_float, ctypes.c_float, ctypes.c_int,
+                                      ctypes.c_int]
     L.fvna_step_noalloc.restype = ctypes.c_int
     L.fvna_step_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Domain), vp, vp,
                                     ctypes.c_double, ctypes.c_double, dp, vp]
@@ -287,11 +288,14 @@ class Solver:
     def launch_count(self) -> int:
         return int(lib().fvna_launch_count(self._h))
 
-    def set_correction(self, net, in_scale: float, out_scale: float) -> None:
-        """Add out_scale * net(in_scale * state) after every step (net=None detaches)."""
+    def set_correction(self, net, in_scale: float, out_scale: float, every: int = 1,
+                       edge_band: int = 0) -> None:
+        """Add out_scale * net(in_scale * state) after every `every`-th step,
+        except within edge_band cells of the domain edges (net=None detaches)."""
         self._net = net
         _check(lib().fvna_set_correction(self._h, net._h if net is not None else None,
-                                         float(in_scale), float(out_scale)),
+                                         float(in_scale), float(out_scale), int(every),
+                                         int(edge_band)),
                "fvna_set_correction")
 
     def close(self):
@@ -363,11 +367,12 @@ class Net:
         return g
 
     def train_step(self, x, target, lr: float, in_scale: float = 1.0, margin: int = 0,
-                   stream=None) -> float:
+                   edges=None, stream=None) -> float:
+        """edges: optional int32 CUDA tensor (B, 4) of per-side margins."""
         B, C, H, W = x.shape
         loss = ctypes.c_double(0.0)
         _check(lib().fvna_net_train_step(self._h, B, H, W, _ptr(x), float(in_scale), _ptr(target),
-                                         int(margin), float(lr), ctypes.byref(loss),
+                                         int(margin), _ptr(edges), float(lr), ctypes.byref(loss),
                                          ctypes.c_void_p(stream or _current_stream())),
                "fvna_net_train_step")
         return loss.value

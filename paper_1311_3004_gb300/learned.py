@@ -35,6 +35,8 @@ class Spec:
     t_train: float     # training runs end here
     t_end: float       # evaluation runs end here
     sample_every: int  # coarse steps between training samples
+    every: int = 1     # the network corrects every `every` coarse steps
+    band: int = 0      # cells next to the domain edges left uncorrected
     nu: float = 0.4
     freq: float = 1.0e6
 
@@ -50,8 +52,8 @@ class Spec:
 
 SMALL = Spec(nz=256, nr=64, cpw=8.0, aperture_m=9e-3, focal_m=18e-3, t_train=30.0, t_end=40.0,
              sample_every=10)
-FULL = Spec(nz=2048, nr=512, cpw=15.0, aperture_m=30e-3, focal_m=60e-3, t_train=100.0,
-            t_end=320.0, sample_every=100)
+FULL = Spec(nz=2048, nr=512, cpw=15.0, aperture_m=30e-3, focal_m=60e-3, t_train=320.0,
+            t_end=320.0, sample_every=200, every=10, band=4)
 
 
 def _solver(spec: Spec, fine: bool, p_surface: float, q0=None, t0: float = 0.0,
@@ -86,8 +88,8 @@ def restrict(torch, pf, dx_fine):
 
 
 def generate(spec: Spec, amplitudes, log=print):
-    """Training samples (X, T): X = one coarse step from the restricted fine
-    state, T = restricted fine state one coarse step later minus X."""
+    """Training samples (X, T): X = `every` coarse steps from the restricted
+    fine state, T = the restricted fine state at the same time minus X."""
     import torch
     xs, ts = [], []
     dxf = spec.workload(True, 1.0).dx
@@ -96,18 +98,19 @@ def generate(spec: Spec, amplitudes, log=print):
         sf, wf = _solver(spec, True, a, steps_per_graph=2 * spec.sample_every)
         qf = torch.empty((3, wf.ny, wf.nx), dtype=torch.float64, device="cuda")
         t_now, k = 0.0, 0
+        k_ = spec.every
         while t_now < spec.t_train:
-            sf.run(max_steps=2 * spec.sample_every - 2)
+            sf.run(max_steps=2 * max(spec.sample_every - k_, 0))
             st = sf.stats(0)
             A = restrict(torch, _pert(torch, sf.q(0, out=qf)), dxf)
             ta = st["t"]
-            sf.run(max_steps=2)
+            sf.run(max_steps=2 * k_)
             B = restrict(torch, _pert(torch, sf.q(0, out=qf)), dxf)
             t_now = sf.stats(0)["t"]
             qa = A.double()
             qa[0] += 1.0
             sc, _ = _solver(spec, False, a, q0=qa, t0=ta)
-            sc.run(max_steps=1)
+            sc.run(max_steps=k_)
             X = _pert(torch, sc.q(0, out=torch.empty_like(qa)))
             sc.close()
             xs.append(X)
@@ -130,55 +133,84 @@ def _init_params(seed: int):
     return np.concatenate(flat).astype(np.float32)
 
 
-def train_net(X, T, steps=1500, batch=8, crop=96, lr=1e-3, margin=4, seed=0, log=print):
+def train_net(X, T, steps=1500, batch=8, crop=96, lr=1e-3, margin=4, seed=0, noise=0.0,
+              importance=False, log=print):
     """Train a fresh network on random crops of (X, T); returns (net, info).
-    in_scale normalises the state, out_scale the residual."""
+    in_scale normalises the state, out_scale the residual.  Crops are drawn
+    with probability proportional to the residual energy they contain (plus
+    a floor) if importance, since the residual is concentrated where the
+    wave is; otherwise uniformly.  With
+    noise > 0 the inputs get Gaussian noise of that many standard deviations
+    of X, so the network tolerates the drift of a corrected run."""
     import torch
+    import torch.nn.functional as F
     g = torch.Generator(device="cpu").manual_seed(seed)
     in_scale = float(1.0 / X.std())
     out_scale = float(T.std())
     net = fvna.Net(_init_params(seed))
     n, _, H, W = X.shape
     ch, cw = min(crop, H), min(crop, W)
+    # residual energy of every crop position (stride 8), as sampling weights
+    e = F.avg_pool2d((T * T).sum(dim=1, keepdim=True), (ch, cw), stride=8)[:, 0]
+    wts = (e + 0.05 * e.mean()).reshape(-1).double().cpu()
+    gh, gw = e.shape[1], e.shape[2]
+    last_i, last_j = H - ch, W - cw
     losses = []
     t0 = time.perf_counter()
     for it in range(steps):
-        idx = torch.randint(0, n, (batch,), generator=g)
-        i0 = torch.randint(0, H - ch + 1, (batch,), generator=g)
-        j0 = torch.randint(0, W - cw + 1, (batch,), generator=g)
+        if importance:
+            pick = torch.multinomial(wts, batch, replacement=True, generator=g)
+            idx = pick // (gh * gw)
+            i0 = torch.clamp((pick // gw) % gh * 8 + torch.randint(0, 8, (batch,), generator=g),
+                             0, last_i)
+            j0 = torch.clamp(pick % gw * 8 + torch.randint(0, 8, (batch,), generator=g),
+                             0, last_j)
+        else:
+            idx = torch.randint(0, n, (batch,), generator=g)
+            i0 = torch.randint(0, H - ch + 1, (batch,), generator=g)
+            j0 = torch.randint(0, W - cw + 1, (batch,), generator=g)
         xb = torch.stack([X[idx[b], :, i0[b]:i0[b] + ch, j0[b]:j0[b] + cw] for b in range(batch)])
         tb = torch.stack([T[idx[b], :, i0[b]:i0[b] + ch, j0[b]:j0[b] + cw] for b in range(batch)])
+        if noise > 0:
+            xb = xb + (noise / in_scale) * torch.randn(xb.shape, generator=g).to(xb.device)
+        # the loss covers the cells at least `margin` from every crop edge;
+        # the correction is applied on the same band of the full field
+        # (at least `margin` from every domain edge)
+        edges = None
         lr_t = lr * (0.1 ** (it / steps))
         losses.append(net.train_step(xb.contiguous(), (tb / out_scale).contiguous(), lr_t,
-                                     in_scale=in_scale, margin=margin))
+                                     in_scale=in_scale, margin=margin, edges=edges))
         if log and (it % max(1, steps // 5) == 0 or it == steps - 1):
-            log(f"  step {it}: loss {losses[-1]:.4e}")
-    info = {"in_scale": in_scale, "out_scale": out_scale,
-            "loss_first": float(np.mean(losses[:20])),
-            "loss_last": float(np.mean(losses[-20:])), "seconds": time.perf_counter() - t0,
+            log(f"  step {it}: loss {np.mean(losses[-50:]):.4e}")
+    info = {"in_scale": in_scale, "out_scale": out_scale, "margin": margin,
+            "loss_first": float(np.mean(losses[:50])),
+            "loss_last": float(np.mean(losses[-50:])), "seconds": time.perf_counter() - t0,
             "steps": steps}
     return net, info
 
 
 def evaluate(spec: Spec, p_surface: float, net=None, info=None, fine_precision=fvna.FP64,
-             t_end=None):
+             t_end=None, gains=(1.0,)):
     """Run coarse (with and without the network) and fine to t_end; return the
     focal peak pressures, errors against the fine run and the run times."""
     import torch
     t_end = spec.t_end if t_end is None else t_end
     out = {}
     dxf = spec.workload(True, 1.0).dx
-    for name, use_net in (("coarse", False), ("coarse_net", True)):
-        if use_net and net is None:
-            continue
+    runs = [("coarse", 0.0)] + ([(f"coarse_net" if g == 1.0 else f"coarse_net_gain{g}", g)
+                                 for g in gains] if net is not None else [])
+    for name, gain in runs:
+        use_net = gain > 0
         s, w = _solver(spec, False, p_surface, steps_per_graph=64)
         if use_net:
-            s.set_correction(net, info["in_scale"], info["out_scale"])
+            s.set_correction(net, info["in_scale"], gain * info["out_scale"], spec.every,
+                             edge_band=spec.band)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.run(t_end=t_end)
+        st = s.run(t_end=t_end, check=False)
         torch.cuda.synchronize()
-        out[name] = {"seconds": time.perf_counter() - t0, "p": torch.from_numpy(s.pressure(0))}
+        out[name] = {"seconds": time.perf_counter() - t0, "p": torch.from_numpy(s.pressure(0)),
+                     "status": st["rc"]}
         s.close()
     s, w = _solver(spec, True, p_surface, precision=fine_precision, steps_per_graph=64)
     torch.cuda.synchronize()
@@ -192,11 +224,15 @@ def evaluate(spec: Spec, p_surface: float, net=None, info=None, fine_precision=f
     peak_f = float(pfr.max())
     res = {"t_end": t_end, "p_surface": p_surface, "focal_peak_fine": peak_f,
            "fine_seconds": out["fine"]["seconds"]}
-    for name in ("coarse", "coarse_net"):
-        if name not in out:
+    for name in out:
+        if name == "fine":
             continue
         p = out[name]["p"].double()
-        res[name] = {"seconds": out[name]["seconds"],
+        if out[name]["status"] != 0:
+            res[name] = {"seconds": out[name]["seconds"], "status": out[name]["status"],
+                         "focal_peak_rel_err": float("inf"), "l2_rel_err": float("inf")}
+            continue
+        res[name] = {"seconds": out[name]["seconds"], "status": 0,
                      "focal_peak": float(p.max()),
                      "focal_peak_rel_err": abs(float(p.max()) - peak_f) / peak_f,
                      "l2_rel_err": float(torch.linalg.norm(p - pfr) / torch.linalg.norm(pfr))}

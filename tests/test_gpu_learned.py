@@ -14,7 +14,7 @@ def test_trained_network_improves_coarse_runs():
     build.build()
     spec = learned.SMALL
     X, T = learned.generate(spec, [0.2e6, 0.35e6, 0.5e6], log=None)
-    net, info = learned.train_net(X, T, steps=600, crop=48, batch=8, log=None)
+    net, info = learned.train_net(X, T, steps=600, crop=48, batch=8, lr=1e-3, log=None)
     assert info["loss_last"] < 0.5 * info["loss_first"]
     res = learned.evaluate(spec, 0.42e6, net, info)
     print(res)
