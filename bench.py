@@ -61,6 +61,10 @@ def parse():
                     default="gaussian",
                     help="gaussian: the headline line; the others print their own line")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile-x", type=int, default=0,
+                    help="x1-sweep tile width (16/32/64; 0: the library's choice)")
+    ap.add_argument("--tile-y", type=int, default=0,
+                    help="x2-sweep tile height (0: the library's choice)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--plain-update", action="store_true",
@@ -226,10 +230,11 @@ def peaks():
 
 
 def measure_precision(torch, fvna, w, precision, steps, warmup, flush, do_flush=True,
-                      compensated=1):
+                      compensated=1, tiles=(0, 0)):
     stream = torch.cuda.current_stream()
     cfg = fvna.make_config(precision=precision, beta=w.beta, delta=w.delta, dx=w.dx,
-                           nu_w=w.nu_w, steps_per_graph=1, compensated=compensated)
+                           nu_w=w.nu_w, steps_per_graph=1, compensated=compensated,
+                           tile_x=tiles[0], tile_y=tiles[1])
     s = fvna.Solver(cfg, [fvna.make_domain(w.nx, w.ny, bc=w.bc)], [w.q0],
                     stream=stream.cuda_stream)
     for _ in range(warmup):
@@ -274,7 +279,8 @@ def run_native(args):
     with ClockSampler(dev_index) as clk:
         per, launches, st = measure_precision(torch, fvna, w, prec, args.steps, args.warmup,
                                               flush, args.flush_mb > 0,
-                                              0 if args.plain_update else 1)
+                                              0 if args.plain_update else 1,
+                                              (args.tile_x, args.tile_y))
     torch.cuda.synchronize()
     step_ms = per.sum(axis=1)
     from paper_1311_3004_gb300.replicas import job_throughput

@@ -42,6 +42,8 @@ extern "C" {
 #define FVNA_ERR_CFL      -5  /* a step ran with nu > nu_max (section 4) */
 #define FVNA_ERR_NAN      -6  /* a wave speed was NaN */
 #define FVNA_ERR_SIZE     -7  /* domain larger than a fixed-size scratch area allows */
+#define FVNA_ERR_TIMEOUT  -8  /* a kernel gave up waiting for one of its own asynchronous
+                                 copies (bounded wait; the run stops, the context stays usable) */
 
 /* ---- enumerations ------------------------------------------------------ */
 enum fvna_precision {
@@ -186,6 +188,11 @@ void fvna_destroy(fvna_ctx *ctx);
 
 /* fvna_strerror -- static text for a status code. */
 const char *fvna_strerror(int code);
+
+/* fvna_last_cuda_error -- the CUDA runtime's text for the last CUDA error
+ * behind an FVNA_ERR_CUDA or FVNA_ERR_OOM return in this process (static
+ * storage, never NULL; "no error" if none).  Not part of the paper's method. */
+const char *fvna_last_cuda_error(void);
 
 /* fvna_riemann -- run the device Roe solver of one x1-sweep interface on n
  * host pairs (section 3.2; fluctuations of eqs. fluc:m, fluc:p), for checks.

@@ -53,12 +53,20 @@ struct fvna_ctx {
   int net_every = 1;
   int net_band = 0;
   __nv_bfloat16 *net_h = nullptr;   // two hidden activation buffers
+  void *d_maps = nullptr;           // binary32: TMA tensor maps of every domain
+  unsigned *d_ctr = nullptr;        // binary32: tile counters of the two sweeps
+  int *d_redo = nullptr;            // binary32: redo counts and lists of the two sweeps
+  int redo_blocks = 1;
+  double *d_budget = nullptr;       // binary32: on-demand budget sums
 };
 
 namespace {
 
+cudaError_t g_last_cuda_error = cudaSuccess;
+
 int cuda_err(cudaError_t e) {
   if (e == cudaSuccess) return FVNA_OK;
+  g_last_cuda_error = e;
   if (e == cudaErrorMemoryAllocation) return FVNA_ERR_OOM;
   return FVNA_ERR_CUDA;
 }
@@ -70,6 +78,7 @@ int cuda_err(cudaError_t e) {
   } while (0)
 
 int status_code(int bits) {
+  if (bits & ST_TIMEOUT) return FVNA_ERR_TIMEOUT;
   if (bits & ST_NONREAL) return FVNA_ERR_NONREAL;
   if (bits & ST_NAN) return FVNA_ERR_NAN;
   if (bits & ST_CFL) return FVNA_ERR_CFL;
@@ -123,22 +132,45 @@ void free_ctx(fvna_ctx *c) {
   cudaFree(c->d_state);
   cudaFree(c->d_stage);
   cudaFree(c->net_h);
+  cudaFree(c->d_maps);
+  cudaFree(c->d_ctr);
+  cudaFree(c->d_redo);
+  cudaFree(c->d_budget);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete c;
 }
 
+// border values of the step: the HIFU drive buffer (binary64 domains) or
+// the ghost ring (binary32 domains with a driven border)
 int enqueue_drives(fvna_ctx *c, cudaStream_t s) {
-  for (int d = 0; d < c->ndom; d++)
+  for (int d = 0; d < c->ndom; d++) {
     if (c->dd[d].drive) CK(launch_drive(c->cfg.precision, c->args, d, c->dd[d].ny, 0, s));
+    if (c->dd[d].ghost32) CK(launch_ghost32(c->args, d, c->dd[d].nx, c->dd[d].ny, 0, s));
+  }
   return FVNA_OK;
+}
+
+// a sweep: binary64 one kernel; binary32 the speculative kernel, then the
+// kernel that redoes the tiles it listed (usually none)
+cudaError_t sweep_x(fvna_ctx *c, cudaStream_t s) {
+  cudaError_t e = launch_sweep_x(c->cfg.precision, c->tile_x, c->args_x, c->blocks_x, s);
+  if (e == cudaSuccess && c->cfg.precision == FVNA_FP32_PERT)
+    e = launch_sweep_x_redo32(c->tile_x, c->args_x, c->redo_blocks, s);
+  return e;
+}
+cudaError_t sweep_y(fvna_ctx *c, cudaStream_t s) {
+  cudaError_t e = launch_sweep_y(c->cfg.precision, c->args_y, c->blocks_y, s);
+  if (e == cudaSuccess && c->cfg.precision == FVNA_FP32_PERT)
+    e = launch_sweep_y_redo32(c->args_y, c->redo_blocks, s);
+  return e;
 }
 
 int enqueue_steps_raw(fvna_ctx *c, cudaStream_t s, int nsteps) {
   for (int i = 0; i < nsteps; i++) {
     int rc = enqueue_drives(c, s);
     if (rc != FVNA_OK) return rc;
-    CK(launch_sweep_x(c->cfg.precision, c->tile_x, c->args_x, c->blocks_x, s));
-    CK(launch_sweep_y(c->cfg.precision, c->args_y, c->blocks_y, s));
+    CK(sweep_x(c, s));
+    CK(sweep_y(c, s));
     if (c->net) {
       const DomDev &d = c->dd[0];
       size_t pix = (size_t)d.nx * d.ny;
@@ -254,6 +286,8 @@ cudaError_t launch_riemann(int p, double beta, int n, const double *qL, const do
 // ---------------------------------------------------------------------------
 extern "C" {
 
+const char *fvna_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda_error); }
+
 const char *fvna_strerror(int code) {
   switch (code) {
     case FVNA_OK: return "ok";
@@ -264,8 +298,44 @@ const char *fvna_strerror(int code) {
     case FVNA_ERR_CFL: return "CFL number above nu_max";
     case FVNA_ERR_NAN: return "NaN wave speed";
     case FVNA_ERR_SIZE: return "domain larger than the fixed scratch area allows";
+    case FVNA_ERR_TIMEOUT: return "a kernel timed out waiting for its own asynchronous copy";
     default: return "unknown status";
   }
+}
+
+// Tile shapes of the binary32 sweeps when the configuration leaves them
+// open.  Each SM works through ceil(tiles / SMs) tiles whose cost grows with
+// the cells a lane marches (tile plus halo); fewer than `want` tiles per SM
+// leave the SM short of warps to overlap, which the cost counts as idle.
+static double tile_cost(long long tiles, int sms, int per_tile, int want) {
+  double per_sm = std::ceil((double)tiles / sms);
+  double fill = std::min(1.0, (double)tiles / sms / want);
+  return per_sm * per_tile / fill;
+}
+static int pick_tile_x32(int n, const fvna_domain *d, int sms) {
+  int best = 64;
+  double best_cost = 1e300;
+  for (int tx : {64, 32, 16}) {
+    int sw = x32_half(tx);
+    long long T = 0;
+    for (int k = 0; k < n; k++)
+      T += (long long)((d[k].ny + XROWS - 1) / XROWS) * ((d[k].nx + 2 * sw - 1) / (2 * sw));
+    double c = tile_cost(T, sms, sw + 4, 7);
+    if (c < best_cost) { best_cost = c; best = tx; }
+  }
+  return best;
+}
+static int pick_tile_y32(int n, const fvna_domain *d, int sms) {
+  int best = 64;
+  double best_cost = 1e300;
+  for (int ty = 8; ty <= 256; ty += 4) {
+    long long T = 0;
+    for (int k = 0; k < n; k++)
+      T += (long long)((d[k].nx + Y32_COLS - 1) / Y32_COLS) * ((d[k].ny + ty - 1) / ty);
+    double c = tile_cost(T, sms, ty + 2 * HALO_Y, 8);
+    if (c < best_cost) { best_cost = c; best = ty; }
+  }
+  return best;
 }
 
 static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
@@ -277,13 +347,34 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   const int prec = cfg->precision;
   const size_t esz = prec == FVNA_FP64 ? sizeof(double) : sizeof(float);
   c->gsteps = cfg->steps_per_graph > 0 ? cfg->steps_per_graph : 32;
-  c->tile_x = cfg->tile_x ? cfg->tile_x : 32;
-  c->tile_y = cfg->tile_y ? cfg->tile_y : 64;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (prec == FVNA_FP64) {
+    c->tile_x = cfg->tile_x ? cfg->tile_x : 32;
+    c->tile_y = cfg->tile_y ? cfg->tile_y : 64;
+  } else {
+    c->tile_x = cfg->tile_x ? cfg->tile_x : pick_tile_x32(n, doms, sms);
+    c->tile_y = cfg->tile_y ? cfg->tile_y : pick_tile_y32(n, doms, sms);
+  }
+  // border values evaluated once per step: binary64 domains driven on the
+  // x1-low border (HIFU) keep a drive buffer; binary32 domains with any
+  // driven border (Taylor, HIFU) a ghost ring
+  auto driven = [&](const fvna_domain &D) {
+    for (int k = 0; k < 4; k++)
+      if (D.bc[k] == BC_TAYLOR) return true;
+    return D.bc[0] == BC_HIFU;
+  };
+  auto border_bytes = [&](const fvna_domain &D) -> size_t {
+    if (prec == FVNA_FP64)
+      return D.bc[0] == BC_HIFU ? (3 * HALO_Y * (size_t)D.ny * esz + 255) / 256 * 256 : 0;
+    return driven(D) ? (ghost_ring_bytes(D.nx, D.ny) + 255) / 256 * 256 : 0;
+  };
   c->kernels_per_step = 3;
-  for (int d = 0; d < n; d++) c->kernels_per_step += doms[d].bc[0] == BC_HIFU ? 1 : 0;
+  for (int d = 0; d < n; d++) c->kernels_per_step += border_bytes(doms[d]) ? 1 : 0;
 
   // state planes: 2 sets x 3 planes per domain, each plane 256-byte aligned,
-  // then the HIFU border buffer of domains driven on the x1-low border
+  // then the domain's border buffer
   std::vector<size_t> offs(n), doffs(n);
   size_t total = 0, max_cells = 0;
   for (int d = 0; d < n; d++) {
@@ -292,7 +383,7 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
     offs[d] = total;
     total += 6 * plane;
     doffs[d] = total;
-    if (doms[d].bc[0] == BC_HIFU) total += (3 * HALO_Y * (size_t)doms[d].ny * esz + 255) / 256 * 256;
+    total += border_bytes(doms[d]);
     max_cells = std::max(max_cells, (size_t)doms[d].nx * doms[d].ny);
   }
   CK(cudaMalloc(&c->d_state, total));
@@ -317,7 +408,9 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
       g.qa[k] = base + k * plane;
       g.qb[k] = base + (3 + k) * plane;
     }
-    g.drive = D.bc[0] == BC_HIFU ? (char *)c->d_state + doffs[d] : nullptr;
+    char *bb = border_bytes(D) ? (char *)c->d_state + doffs[d] : nullptr;
+    g.drive = prec == FVNA_FP64 ? bb : nullptr;
+    g.ghost32 = prec == FVNA_FP64 ? nullptr : bb;
   }
   CK(cudaMemsetAsync(c->d_state, 0, total, c->stream));
   CK(cudaMalloc(&c->d_dd, sizeof(DomDev) * n));
@@ -333,14 +426,30 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   CK(cudaMemcpyAsync(c->d_scal, sc.data(), sizeof(DomScal) * n, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMallocHost(&c->h_scal, sizeof(DomScal) * n));
 
-  // warp tiles
-  std::vector<Tile> tx, ty;
+  // warp tiles (binary64: 32 rows x tile_x and 30 columns x tile_y;
+  // binary32: 32 rows x 2 halves and 60 columns x tile_y)
+  // (binary32: the tiles that touch a domain border come first; they take
+  // longer and the sweeps hand tiles out in list order)
+  std::vector<Tile> tx, ty, txb, tyb;
+  const int sw = x32_half(c->tile_x);
+  const int xstep = prec == FVNA_FP64 ? c->tile_x : 2 * sw;
+  const int ystep = prec == FVNA_FP64 ? YCOLS : Y32_COLS;
   for (int d = 0; d < n; d++) {
-    for (int y = 0; y < doms[d].ny; y += XROWS)
-      for (int x = 0; x < doms[d].nx; x += c->tile_x) tx.push_back(Tile{d, x, y, 0});
-    for (int y = 0; y < doms[d].ny; y += c->tile_y)
-      for (int x = 0; x < doms[d].nx; x += YCOLS) ty.push_back(Tile{d, x, y, 0});
+    const int nx = doms[d].nx, ny = doms[d].ny;
+    for (int y = 0; y < ny; y += XROWS)
+      for (int x = 0; x < nx; x += xstep) {
+        bool b = prec == FVNA_FP32_PERT && (x == 0 || x + 2 * sw + 2 > nx || y + XROWS > ny);
+        (b ? txb : tx).push_back(Tile{d, x, y, 0});
+      }
+    for (int y = 0; y < ny; y += c->tile_y)
+      for (int x = 0; x < nx; x += ystep) {
+        bool b = prec == FVNA_FP32_PERT &&
+                 (x < 2 || x + Y32_COLS + 2 > nx || y < HALO_Y || y + c->tile_y + HALO_Y > ny);
+        (b ? tyb : ty).push_back(Tile{d, x, y, 0});
+      }
   }
+  tx.insert(tx.begin(), txb.begin(), txb.end());
+  ty.insert(ty.begin(), tyb.begin(), tyb.end());
   c->ntx = (int)tx.size();
   c->nty = (int)ty.size();
   CK(cudaMalloc(&c->d_tx, sizeof(Tile) * tx.size()));
@@ -351,13 +460,22 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   // kernel set-up and persistent grid sizes
   const int comp = prec == FVNA_FP32_PERT && cfg->compensated ? 1 : 0;
   CK(prepare_kernels(prec, c->tile_x, cfg->limiter, comp));
-  int dev = 0, sms = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int occx = std::max(1, occupancy_x(prec, c->tile_x, cfg->limiter, comp));
   int occy = std::max(1, occupancy_y(prec, cfg->limiter, comp));
-  c->blocks_x = std::max(1, std::min((c->ntx + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, occx * sms));
-  c->blocks_y = std::max(1, std::min((c->nty + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, occy * sms));
+  const int wpb = prec == FVNA_FP64 ? WARPS_PER_BLOCK : 1;  // binary32: one warp per block
+  c->blocks_x = std::max(1, std::min((c->ntx + wpb - 1) / wpb, occx * sms));
+  c->blocks_y = std::max(1, std::min((c->nty + wpb - 1) / wpb, occy * sms));
+  if (prec == FVNA_FP32_PERT) {
+    CK(build_maps_fp32(c->dd.data(), n, c->tile_x, &c->d_maps, c->stream));
+    CK(cudaMalloc(&c->d_budget, 3 * sizeof(double)));
+    CK(cudaMalloc(&c->d_ctr, 2 * sizeof(unsigned)));
+    CK(cudaMemsetAsync(c->d_ctr, 0, 2 * sizeof(unsigned), c->stream));
+    CK(cudaMalloc(&c->d_redo, (2 + (size_t)c->ntx + c->nty) * sizeof(int)));
+    CK(cudaMemsetAsync(c->d_redo, 0, 2 * sizeof(int), c->stream));
+    CK(prepare_kernels_redo32(c->tile_x, cfg->limiter, comp));
+    c->redo_blocks = sms;
+    c->kernels_per_step += 2;
+  }
 
   StepArgs &a = c->args;
   std::memset(&a, 0, sizeof a);
@@ -369,12 +487,20 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   a.limiter = cfg->limiter; a.geometry = cfg->geometry; a.sweeps = cfg->sweeps;
   a.tile_y = c->tile_y;
   a.compensated = comp;
+  a.tmaps = c->d_maps;
+  a.counters = c->d_ctr;
+  a.redo = c->d_redo;
   c->args_x = a;
   c->args_x.tiles = c->d_tx;
   c->args_x.ntiles = c->ntx;
+  c->args_x.sweep = 0;
+  c->args_x.redo_off = 2;
   c->args_y = a;
   c->args_y.tiles = c->d_ty;
   c->args_y.ntiles = c->nty;
+  c->args_y.sweep = 1;
+  c->args_y.redo_off = 2 + c->ntx;
+
 
   // initial state
   if (!q0_on_device) {
@@ -496,6 +622,16 @@ int fvna_fields(fvna_ctx *c, int domain, int what, void *dst, size_t bytes, int 
   const DomScal &S = c->h_scal[domain];
   if (what == FVNA_FIELD_BUDGET) {
     if (bytes < 3 * sizeof(double)) return FVNA_ERR_ARG;
+    if (c->cfg.precision == FVNA_FP32_PERT) {
+      // binary32: summed on demand from the stored state, in binary64
+      double b[3];
+      CK(launch_budget_fp32(c->dd[domain], c->d_budget, c->stream));
+      CK(cudaMemcpyAsync(b, c->d_budget, sizeof b, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      if (dst_on_device) CK(cudaMemcpy(dst, b, sizeof b, cudaMemcpyHostToDevice));
+      else std::memcpy(dst, b, sizeof b);
+      return FVNA_OK;
+    }
     if (dst_on_device) CK(cudaMemcpy(dst, S.budget, 3 * sizeof(double), cudaMemcpyHostToDevice));
     else std::memcpy(dst, S.budget, 3 * sizeof(double));
     return FVNA_OK;
@@ -525,9 +661,9 @@ int fvna_step_timed(fvna_ctx *c, float ms[3]) {
   if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->stream);
   if (e == cudaSuccess && enqueue_drives(c, c->stream) != FVNA_OK) e = cudaErrorUnknown;
   if (e == cudaSuccess)
-    e = launch_sweep_x(c->cfg.precision, c->tile_x, c->args_x, c->blocks_x, c->stream);
+    e = sweep_x(c, c->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
-  if (e == cudaSuccess) e = launch_sweep_y(c->cfg.precision, c->args_y, c->blocks_y, c->stream);
+  if (e == cudaSuccess) e = sweep_y(c, c->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->stream);
   if (e == cudaSuccess) e = launch_advance(c->args, c->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[3], c->stream);

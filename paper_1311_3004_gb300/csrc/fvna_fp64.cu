@@ -11,6 +11,7 @@
 #define POLICY P64
 #define SUFFIX fp64
 #define HAS_COMP 0
+#define FVNA_PRECISION_SWEEPS 1
 #include "fvna_precision.inc"
 
 namespace fvna {
@@ -38,6 +39,7 @@ __global__ void k_advance(StepArgs A) {
   double smax = __longlong_as_double((long long)S->smax_bits);
   int st = 0;
   if (S->status_bits & ST_NONREAL) st |= ST_NONREAL;
+  if (S->status_bits & ST_TIMEOUT) st |= ST_TIMEOUT;
   if (smax != smax) st |= ST_NAN;
   double dt = S->dt;
   if (A.sweeps & 3) {

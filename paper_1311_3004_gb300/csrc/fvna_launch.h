@@ -58,4 +58,21 @@ cudaError_t prepare_kernels_fp32(int tile_x, int lim, int comp);
 int occupancy_x_fp32(int tile_x, int lim, int comp);
 int occupancy_y_fp32(int lim, int comp);
 
+// binary32 sweeps (fvna_fp32.cu): x1 tiles are 32 rows x 2*x32_half(tile_x)
+// cells, x2 tiles 60 columns x tile_y rows; TMA tensor maps of every domain
+// (device array, cudaFree to release); budgets on demand (sum of the state,
+// binary64, into dst[3] on the device)
+int x32_half(int tile_x);
+constexpr int Y32_COLS = 60;
+cudaError_t build_maps_fp32(const DomDev *dd, int n, int tile_x, void **d_maps, cudaStream_t s);
+cudaError_t launch_budget_fp32(const DomDev &d, double *dst, cudaStream_t s);
+// second kernels of the binary32 sweeps (tiles listed for the general split)
+cudaError_t prepare_kernels_redo32(int tile_x, int lim, int comp);
+cudaError_t launch_sweep_x_redo32(int tile_x, const StepArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_sweep_y_redo32(const StepArgs &a, int blocks, cudaStream_t s);
+// ghost ring of a binary32 domain with a driven border (bytes), and the
+// kernel that fills it with the analytic border values of the current step
+size_t ghost_ring_bytes(int nx, int ny);
+cudaError_t launch_ghost32(const StepArgs &a, int dom, int nx, int ny, int always, cudaStream_t s);
+
 }  // namespace fvna

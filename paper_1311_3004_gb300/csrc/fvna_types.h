@@ -7,7 +7,8 @@ namespace fvna {
 
 enum { BC_PERIODIC = 0, BC_EXTRAP = 1, BC_REFLECT = 2, BC_TAYLOR = 3, BC_HIFU = 4 };
 enum { LIM_MC = 0, LIM_NONE = 1, LIM_LW = 2 };
-enum { ST_NONREAL = 1, ST_CFL = 2, ST_NAN = 4 };
+// ST_TIMEOUT: a kernel gave up waiting for one of its own asynchronous copies
+enum { ST_NONREAL = 1, ST_CFL = 2, ST_NAN = 4, ST_TIMEOUT = 8 };
 
 // Halo widths: the x1 sweep reads 2 cells beyond its tile (the limiter looks
 // one interface upwind), the x2 sweep with the fused source reads 3.
@@ -34,6 +35,8 @@ struct DomDev {
   void *qb[3];                  // planes after the x1 sweep
   void *drive;                  // HIFU border values of the current step, 3 planes of
                                 // HALO_Y x ny (ghost column -1-k at k*ny + row), or NULL
+  void *ghost32;                // binary32 domains with a driven border: the ghost ring
+                                // (fvna_sweeps32.cuh), or NULL
 };
 
 // Per-domain scalars that evolve on the device (one step = K1, K2, K3).
@@ -70,6 +73,11 @@ struct StepArgs {
   int limiter, geometry, sweeps, tile_y;
   int compensated;               // binary32 update with error-free two-sums
   int pad_;
+  const void *tmaps;             // binary32 sweeps: TMA tensor maps, one set per domain
+  unsigned *counters;            // binary32 sweeps: next-tile counters of the x1 and x2 sweeps
+  int *redo;                     // binary32 sweeps: redo counts of the two sweeps, then lists
+  int redo_off;                  // offset of this sweep's redo list in redo
+  int sweep;                     // 0: x1 sweep, 1: x2 sweep
 };
 
 }  // namespace fvna

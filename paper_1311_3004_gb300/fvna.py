@@ -26,13 +26,17 @@ FIELD_Q, FIELD_PRESSURE, FIELD_BUDGET, FIELD_STATS = 0, 1, 2, 3
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONREAL, ERR_CFL, ERR_NAN = 0, -1, -2, -3, -4, -5, -6
 ERR_SIZE = -7
+ERR_TIMEOUT = -8
 NOALLOC_MAX_CELLS = 524288
 
 
 class FvnaError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
-        super().__init__(f"{where}: {strerror(code)} ({code})")
+        msg = f"{where}: {strerror(code)} ({code})"
+        if code in (ERR_CUDA, ERR_OOM):
+            msg += f" [{lib().fvna_last_cuda_error().decode()}]"
+        super().__init__(msg)
 
 
 class Config(ctypes.Structure):
@@ -66,6 +70,7 @@ class Stats(ctypes.Structure):
 
 SYMBOLS = ["fvna_init", "fvna_step", "fvna_run", "fvna_sync", "fvna_fields",
            "fvna_step_timed", "fvna_launch_count", "fvna_destroy", "fvna_strerror", "fvna_riemann",
+           "fvna_last_cuda_error",
            "fvna_step_noalloc", "fvna_autotune", "fvna_net_create", "fvna_net_params",
            "fvna_net_forward", "fvna_net_backward", "fvna_net_train_step", "fvna_net_destroy",
            "fvna_set_correction"]
@@ -103,6 +108,8 @@ def lib():
     L.fvna_destroy.argtypes = [vp]
     L.fvna_strerror.restype = ctypes.c_char_p
     L.fvna_strerror.argtypes = [ctypes.c_int]
+    L.fvna_last_cuda_error.restype = ctypes.c_char_p
+    L.fvna_last_cuda_error.argtypes = []
     L.fvna_autotune.restype = ctypes.c_int
     L.fvna_autotune.argtypes = [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(Domain),
                                 ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, vp, ctypes.c_int,

@@ -309,6 +309,29 @@ def test_fp32_borders_against_fp64(bc):
     assert peak <= 1e-5 and l2 <= 1e-5, (peak, l2)
 
 
+@pytest.mark.parametrize("flow", [(0.75, 0.0), (0.0, 0.75)])
+def test_fp32_faces_that_are_not_subsonic(flow):
+    """A uniform flow along x1 or x2 fast enough that the second family
+    moves the same way as the first (this system has c^2 = 1 - u^2 + ...,
+    so that is 1/sqrt(2) < |u| < 1), with a small perturbation on top: the
+    binary32 sweep along the flow marches its tiles with the subsonic split
+    first, finds faces where it does not hold and marches those tiles again
+    with the general split; the result matches the oracle, whose split is
+    the general one everywhere."""
+    n = 80
+    q = wl.random_smooth(n, n, 1e-3, seed=61)
+    q[1] += flow[0] * q[0]
+    q[2] += flow[1] * q[0]
+    c = Case(n, n, q, bc=(P, P, P, P), beta=3.5, delta=1e-3, dx=1.0 / 32)
+    qo, so = run_oracle(c, 60)
+    assert so["status"] == 0 and so["smax"] > 1.3
+    qg, sg = run_gpu(c, 60, precision=fvna.FP32_PERT)
+    assert sg["rc"] == 0 and sg["steps"] == so["step"]
+    assert pert_rel_linf(qg, qo) <= 1e-5
+    q64, _ = run_gpu(c, 60)
+    assert pert_rel_linf(q64, qo) <= TOL64
+
+
 # ------------------------------------------------------------------ full size
 
 def test_full_size_gaussian_parity_first_steps():
