@@ -325,15 +325,17 @@ static int pick_tile_x32(int n, const fvna_domain *d, int sms) {
   }
   return best;
 }
+// x2 sweep: each warp marches its columns row after row, so the sweep runs
+// at the pace of its warps' latency; heights whose marched rows (ty + 6)
+// fill whole 8-row chunks, the largest that still gives every resident warp
+// (about 12 per SM) two tiles.
 static int pick_tile_y32(int n, const fvna_domain *d, int sms) {
-  int best = 64;
-  double best_cost = 1e300;
-  for (int ty = 8; ty <= 256; ty += 4) {
+  int best = 10;
+  for (int ty = 10; ty <= 250; ty += 8) {
     long long T = 0;
     for (int k = 0; k < n; k++)
       T += (long long)((d[k].nx + Y32_COLS - 1) / Y32_COLS) * ((d[k].ny + ty - 1) / ty);
-    double c = tile_cost(T, sms, ty + 2 * HALO_Y, 8);
-    if (c < best_cost) { best_cost = c; best = ty; }
+    if (T >= 2LL * 12 * sms) best = ty;
   }
   return best;
 }

@@ -31,7 +31,10 @@ constexpr int X32_ROWS = 32;
 #ifndef X32_MINBLOCKS
 #define X32_MINBLOCKS 1
 #endif
-constexpr int Y32_STAGES = 3;
+#ifndef FVNA_Y32_STAGES
+#define FVNA_Y32_STAGES 2
+#endif
+constexpr int Y32_STAGES = FVNA_Y32_STAGES;
 // resident x2-sweep warps per SM the register allocator plans for (the
 // shared-memory ring allows 11)
 #ifndef Y32_MINBLOCKS
