@@ -31,6 +31,9 @@ constexpr int X32_ROWS = 32;
 #ifndef X32_MINBLOCKS
 #define X32_MINBLOCKS 1
 #endif
+#ifndef FVNA_Y_UNROLL
+#define FVNA_Y_UNROLL 2   // rows of the x2 sweep's plain loop unrolled together (measured best)
+#endif
 #ifndef FVNA_Y32_STAGES
 #define FVNA_Y32_STAGES 2
 #endif
@@ -686,8 +689,8 @@ __device__ __forceinline__ int y32_tile(const StepArgs &A, const DomDev &D, DomS
     const bool plain_chunk = ysweep && c > 0 && rows == YRB && x0 >= 2 && x0 + YW + 2 <= D.nx &&
                              r0 >= 0 && r0 + YRB <= D.ny && r0 - 2 > 0;
     if (plain_chunk) {
-      // four rows at a time, so the compiler can overlap consecutive rows
-#pragma unroll 4
+      // several rows at a time, so the compiler can overlap consecutive rows
+      FVNA_UNROLL(FVNA_Y_UNROLL)
       for (int i = 0; i < YRB; i++) {
         const int j = c * YRB + i;
         const unsigned char *rp = st + i * (YBOX * 4) + (2 + 2 * lane) * 4;
