@@ -181,6 +181,14 @@ __device__ __forceinline__ int take_tile(unsigned *ctr, int lane) {
   if (lane == 0) t = atomicAdd(ctr, 1u);
   return (int)__shfl_sync(0xffffffffu, t, 0);
 }
+// the same in two halves: the atomic is issued when a tile starts and its
+// result broadcast when the tile ends, so the march hides its latency
+__device__ __forceinline__ unsigned take_tile_issue(unsigned *ctr, int lane) {
+  return lane == 0 ? atomicAdd(ctr, 1u) : 0u;
+}
+__device__ __forceinline__ int take_tile_collect(unsigned t) {
+  return (int)__shfl_sync(0xffffffffu, t, 0);
+}
 
 // error exit of a failed wait: flag the domain, let the copy land, stop
 __device__ __forceinline__ void wait_failed(DomScal *S, uint64_t *bar, unsigned parity, int lane) {
@@ -389,15 +397,20 @@ __global__ void __launch_bounds__(32, X32_MINBLOCKS) k_sweep_x32(StepArgs A) {
   __syncwarp();
   unsigned phase = 0;
   const bool xsweep = (A.sweeps & 1) != 0;
-  int wn = REDO ? (int)blockIdx.x : take_tile(&A.counters[0], lane);
   const int nt = REDO ? nredo : A.ntiles;
-  for (int it = wn; it < nt; it = wn) {
-    wn = REDO ? it + (int)gridDim.x : take_tile(&A.counters[0], lane);
+  int it = REDO ? (int)blockIdx.x : take_tile(&A.counters[0], lane);
+  while (it < nt) {
+    const unsigned tn = REDO ? 0u : take_tile_issue(&A.counters[0], lane);
     const int w = REDO ? A.redo[A.redo_off + it] : it;
+    const int cur = it;
     const Tile tl = A.tiles[w];
     const DomDev &D = A.doms[tl.dom];
     DomScal *S = A.scal + tl.dom;
-    if (S->done) continue;
+    it = 0;  // set from tn at the end of the body
+    if (S->done) {
+      it = REDO ? cur + (int)gridDim.x : take_tile_collect(tn);
+      continue;
+    }
     const Maps &M = maps[tl.dom];
     const int x0 = tl.x0, y0 = tl.y0;
     if (lane == 0) {
@@ -417,6 +430,7 @@ __global__ void __launch_bounds__(32, X32_MINBLOCKS) k_sweep_x32(StepArgs A) {
     }
     phase ^= 1;
     bool store = true;
+    it = REDO ? cur + (int)gridDim.x : take_tile_collect(tn);
     if (xsweep) {
       if (REDO) {
         x2::x32_tile<SW, LIM, COMP, true, false>(A, D, S, mainb, halo, x0, y0, lane);
@@ -755,15 +769,19 @@ __global__ void __launch_bounds__(32, Y32_MINBLOCKS) k_sweep_y32(StepArgs A) {
   }
   __syncwarp();
   unsigned used = 0;
-  int wn = REDO ? (int)blockIdx.x : take_tile(&A.counters[1], lane);
   const int nt = REDO ? nredo : A.ntiles;
-  for (int it = wn; it < nt; it = wn) {
-    wn = REDO ? it + (int)gridDim.x : take_tile(&A.counters[1], lane);
+  int it = REDO ? (int)blockIdx.x : take_tile(&A.counters[1], lane);
+  while (it < nt) {
+    const unsigned tn = REDO ? 0u : take_tile_issue(&A.counters[1], lane);
     const int w = REDO ? A.redo[A.redo_off + it] : it;
+    const int cur = it;
     const Tile tl = A.tiles[w];
     const DomDev &D = A.doms[tl.dom];
     DomScal *S = A.scal + tl.dom;
-    if (S->done) continue;
+    if (S->done) {
+      it = REDO ? cur + (int)gridDim.x : take_tile_collect(tn);
+      continue;
+    }
     const int x0 = tl.x0, y0 = tl.y0;
     // one code path for all tiles (border rules are per-row branches that
     // chunks away from the domain edges skip)
@@ -773,6 +791,7 @@ __global__ void __launch_bounds__(32, Y32_MINBLOCKS) k_sweep_y32(StepArgs A) {
                                                    lane);
     if (rc == 2 && lane == 0) A.redo[A.redo_off + atomicAdd(&A.redo[1], 1)] = w;
     if (rc == 1) break;
+    it = REDO ? cur + (int)gridDim.x : take_tile_collect(tn);
   }
 }
 
