@@ -363,7 +363,7 @@ __device__ __forceinline__ bool x32_tile(const StepArgs &A, const DomDev &D, Dom
     put(SW / 4 - 1);
   }
   fence_async();
-  if (SPEC && __any_sync(0xffffffffu, m.acc.sub.x <= 0.f || m.acc.sub.y <= 0.f)) return false;
+  if (SPEC && !spec_held(m.acc)) return false;
   flush_acc(m.acc, S, lane);
   return true;
 }
@@ -700,12 +700,31 @@ __device__ __forceinline__ int y32_tile(const StepArgs &A, const DomDev &D, DomS
     // inside the domain (no ghost, no override, every row stored by lanes
     // 1..30)
     const int r0 = y0 - HALO_Y + c * YRB;
-    const bool plain_chunk = ysweep && c > 0 && rows == YRB && x0 >= 2 && x0 + YW + 2 <= D.nx &&
+    const bool plain_chunk = ysweep && rows == YRB && x0 >= 2 && x0 + YW + 2 <= D.nx &&
                              r0 >= 0 && r0 + YRB <= D.ny && r0 - 2 > 0;
+    // rows [0, g_end) take the general path (border rules, start of the
+    // march in the first chunk), the rest the plain one
+    const int g_end = plain_chunk ? (c == 0 ? 4 : 0) : rows;
+    for (int i = 0; i < g_end; i++) {
+      const int j = c * YRB + i;
+      Cell q = fetch(i, j);
+      if (!ysweep) {
+        if (j >= 2 && j <= nrows - 3)
+          ysink<true>(src, A, D, x0, y0, TY, lane, y0 - HALO_Y + j, q.a, q.c, q.b, source, axi,
+                      coef, dt32, ca, cb, qo);
+        continue;
+      }
+      bool kin = j >= klo && j <= khi, nin = j >= nlo && j <= nhi;
+      bool got = m.template push<true>(j, q, out, kin && ca.upd, kin && cb.upd, nin && ca.upd,
+                                       nin && cb.upd, j - 1 >= glo && j - 1 <= ghi);
+      if (got)
+        ysink<true>(src, A, D, x0, y0, TY, lane, y0 - HALO_Y + j - 2, out.a, out.c, out.b, source,
+                    axi, coef, dt32, ca, cb, qo);
+    }
     if (plain_chunk) {
       // several rows at a time, so the compiler can overlap consecutive rows
       FVNA_UNROLL(FVNA_Y_UNROLL)
-      for (int i = 0; i < YRB; i++) {
+      for (int i = g_end; i < YRB; i++) {
         const int j = c * YRB + i;
         const unsigned char *rp = st + i * (YBOX * 4) + (2 + 2 * lane) * 4;
         Cell q;
@@ -716,23 +735,6 @@ __device__ __forceinline__ int y32_tile(const StepArgs &A, const DomDev &D, DomS
         ysink<false>(src, A, D, x0, y0, TY, lane, y0 - HALO_Y + j - 2, o.a, o.c, o.b, source, axi,
                      coef, dt32, ca, cb, qo);
       }
-    } else {
-      for (int i = 0; i < rows; i++) {
-        const int j = c * YRB + i;
-        Cell q = fetch(i, j);
-        if (!ysweep) {
-          if (j >= 2 && j <= nrows - 3)
-            ysink<true>(src, A, D, x0, y0, TY, lane, y0 - HALO_Y + j, q.a, q.c, q.b, source, axi,
-                        coef, dt32, ca, cb, qo);
-          continue;
-        }
-        bool kin = j >= klo && j <= khi, nin = j >= nlo && j <= nhi;
-        bool got = m.template push<true>(j, q, out, kin && ca.upd, kin && cb.upd, nin && ca.upd,
-                                         nin && cb.upd, j - 1 >= glo && j - 1 <= ghi);
-        if (got)
-          ysink<true>(src, A, D, x0, y0, TY, lane, y0 - HALO_Y + j - 2, out.a, out.c, out.b, source,
-                      axi, coef, dt32, ca, cb, qo);
-      }
     }
     // every lane's shared-memory reads of this stage are ordered before its
     // next TMA fill
@@ -740,8 +742,7 @@ __device__ __forceinline__ int y32_tile(const StepArgs &A, const DomDev &D, DomS
     __syncwarp();
     if (lane == 0 && c + Y32_STAGES < nch) issue(c + Y32_STAGES);
   }
-  if (SPEC && ysweep && __any_sync(0xffffffffu, m.acc.sub.x <= 0.f || m.acc.sub.y <= 0.f))
-    return 2;
+  if (SPEC && ysweep && !spec_held(m.acc)) return 2;
   if (ysweep) flush_acc(m.acc, S, lane);
   return 0;
 }

@@ -150,9 +150,14 @@ __device__ __forceinline__ void zof(const Cell &q, V &zb, V &zc) {
 }
 
 // Roe average, speeds and waves between L and R.  bm1 = beta - 1.  Returns
-// c^2 = 1 + (D - 1) (negative: non-real speeds).
+// c^2 = 1 + (D - 1) (negative: non-real speeds) and D - 1 in dm.  SERIES:
+// 1/c from its Taylor series in D - 1 (valid for |D - 1| < DM_SERIES, where
+// its truncation error is below 2e-10; the march records max |D - 1| and a
+// tile beyond that range is redone without SERIES).
+constexpr float DM_SERIES = 0.03f;
+template <bool SERIES>
 __device__ __forceinline__ V roe(V bm1, const Cell &L, V zbL, V zcL, const Cell &R, V zbR, V zcR,
-                                 Face &F) {
+                                 Face &F, V &dm_out) {
   V S1 = add(L.a, R.a);           // 2 (Z1 - 1)
   V S2 = add(zbL, zbR);           // 2 Z2
   V S3 = add(zcL, zcR);           // 2 Z3
@@ -162,13 +167,25 @@ __device__ __forceinline__ V roe(V bm1, const Cell &L, V zbL, V zcL, const Cell 
   V tt = sub(u, S2);              // u - 2 Z2
   V dm = fma(u, tt, mul(bm1, S1));  // D - 1 = u^2 - 2 Z2 u + beta2 (Z1 - 1)
   V c2 = add(dm, vs(1.f));
-  // c - 1 = dm / (1 + sqrt(1 + dm)) keeps the relative precision of dm, so
-  // c = 1 + (c - 1) is rounded once, and 1/c gets one Newton step: both set
-  // the propagation speed of every wave, where an error of the hardware
-  // approximations (~1e-7, one-signed) would add up step after step
-  V c = add(mul(dm, rcp(fma(c2, rsqrt(c2), vs(1.f)))), vs(1.f));
-  V rc = rcp(c);
-  rc = fma(rc, fma(make_float2(-c.x, -c.y), rc, vs(1.f)), rc);
+  dm_out = dm;
+  V c, rc;
+  if (SERIES) {
+    // 1/sqrt(1 + dm) = 1 - dm/2 + 3dm^2/8 - 5dm^3/16 + 35dm^4/128 - 63dm^5/256
+    rc = fma(dm, vs(-63.f / 256.f), vs(35.f / 128.f));
+    rc = fma(dm, rc, vs(-5.f / 16.f));
+    rc = fma(dm, rc, vs(3.f / 8.f));
+    rc = fma(dm, rc, vs(-0.5f));
+    rc = fma(dm, rc, vs(1.f));
+    c = fma(dm, rc, rc);   // (1 + dm) / sqrt(1 + dm), without rounding 1 + dm first
+  } else {
+    // c - 1 = dm / (1 + sqrt(1 + dm)) keeps the relative precision of dm, so
+    // c = 1 + (c - 1) is rounded once, and 1/c gets one Newton step: both set
+    // the propagation speed of every wave, where an error of the hardware
+    // approximations (~1e-7, one-signed) would add up step after step
+    c = add(mul(dm, rcp(fma(c2, rsqrt(c2), vs(1.f)))), vs(1.f));
+    rc = rcp(c);
+    rc = fma(rc, fma(make_float2(-c.x, -c.y), rc, vs(1.f)), rc);
+  }
   V nc1 = sub(c, u);
   F.u = u;
   F.s0 = add(u, c);
@@ -315,8 +332,12 @@ template <bool COMP> __device__ __forceinline__ V update(V q, V Pl, V Mr, V nlam
 // smallest c^2 (negative: non-real speeds somewhere) and the smallest
 // min(s0, -s1) (not positive: a face that is not subsonic).
 struct Acc {
-  V smax, c2min, sub;
+  V smax, c2min, sub, dmax;
 };
+__device__ __forceinline__ void acc_dm(Acc &A, V dm) {
+  A.dmax.x = max3_abs_nan(A.dmax.x, dm.x, 0.f);
+  A.dmax.y = max3_abs_nan(A.dmax.y, dm.y, 0.f);
+}
 __device__ __forceinline__ void acc_face(Acc &A, const Face &F, V c2) {
   A.smax.x = max3_abs_nan(A.smax.x, F.s0.x, F.s1.x);
   A.smax.y = max3_abs_nan(A.smax.y, F.s0.y, F.s1.y);
@@ -333,6 +354,14 @@ __device__ __forceinline__ void acc_face_masked(Acc &A, const Face &F, V c2, boo
   if (ny_) A.c2min.y = fminf(A.c2min.y, c2.y);
   A.sub.x = min3(A.sub.x, F.s0.x, -F.s1.x);
   A.sub.y = min3(A.sub.y, F.s0.y, -F.s1.y);
+}
+
+// Did a speculative march stay within its assumptions (every face subsonic,
+// |D - 1| inside the series range)?  NaN counts as within (it is reported
+// through max |s|).
+__device__ __forceinline__ bool spec_held(const Acc &A) {
+  bool bad = A.sub.x <= 0.f || A.sub.y <= 0.f || A.dmax.x >= DM_SERIES || A.dmax.y >= DM_SERIES;
+  return !__any_sync(0xffffffffu, bad);
 }
 
 // ---------------------------------------------------------------------------
@@ -356,6 +385,7 @@ template <int LIM, bool COMP, bool SPEC> struct March {
     acc.smax = vs(0.f);
     acc.c2min = vs(1.f);
     acc.sub = vs(1.f);
+    acc.dmax = vs(0.f);
   }
   // MASK: per-face accounting masks (border tiles); fo: first-order face
   template <bool MASK>
@@ -369,9 +399,11 @@ template <int LIM, bool COMP, bool SPEC> struct March {
       return false;
     }
     Face f;
-    V c2v = roe(bm1, c1, zb1, zc1, q, zb, zc, f);
+    V dm;
+    V c2v = roe<SPEC>(bm1, c1, zb1, zc1, q, zb, zc, f, dm);
     if (MASK) acc_face_masked(acc, f, c2v, sx, sy, nx_, ny_);
     else acc_face(acc, f, c2v);
+    if (SPEC) acc_dm(acc, dm);
     if (j >= 3) {
       // flux of face j-1 (neighbours: faces j-2 and j)
       V P[3], Mr[3];
@@ -398,9 +430,11 @@ template <int LIM, bool COMP, bool SPEC> struct March {
     V zb, zc;
     zof(q, zb, zc);
     Face f;
-    V c2v = roe(bm1, c1, zb1, zc1, q, zb, zc, f);
+    V dm;
+    V c2v = roe<SPEC>(bm1, c1, zb1, zc1, q, zb, zc, f, dm);
     if (MASK) acc_face_masked(acc, f, c2v, sx, sy, nx_, ny_);
     else acc_face(acc, f, c2v);
+    if (SPEC) acc_dm(acc, dm);
     V P[3], Mr[3];
     flux<LIM, SPEC>(fm, fl, f, nhlam, fo_prev, P, Mr);
     Cell out;
