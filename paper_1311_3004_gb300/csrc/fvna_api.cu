@@ -180,7 +180,7 @@ int enqueue_steps_raw(fvna_ctx *c, cudaStream_t s, int nsteps) {
                             c->net_h, c->net_h + pix * 32, s, &c->d_scal[0].done,
                             &c->d_scal[0].step, c->net_every, c->net_band));
     }
-    CK(launch_advance(c->args, s));
+    if (!c->args_y.fold_advance) CK(launch_advance(c->args, s));
   }
   return FVNA_OK;
 }
@@ -470,13 +470,13 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   if (prec == FVNA_FP32_PERT) {
     CK(build_maps_fp32(c->dd.data(), n, c->tile_x, &c->d_maps, c->stream));
     CK(cudaMalloc(&c->d_budget, 3 * sizeof(double)));
-    CK(cudaMalloc(&c->d_ctr, 2 * sizeof(unsigned)));
-    CK(cudaMemsetAsync(c->d_ctr, 0, 2 * sizeof(unsigned), c->stream));
+    CK(cudaMalloc(&c->d_ctr, 3 * sizeof(unsigned)));
+    CK(cudaMemsetAsync(c->d_ctr, 0, 3 * sizeof(unsigned), c->stream));
     CK(cudaMalloc(&c->d_redo, (2 + (size_t)c->ntx + c->nty) * sizeof(int)));
     CK(cudaMemsetAsync(c->d_redo, 0, 2 * sizeof(int), c->stream));
     CK(prepare_kernels_redo32(c->tile_x, cfg->limiter, comp));
     c->redo_blocks = sms;
-    c->kernels_per_step += 2;
+    c->kernels_per_step += 1;   // two second kernels; the step end runs in one of them
   }
 
   StepArgs &a = c->args;
@@ -502,6 +502,7 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   c->args_y.ntiles = c->nty;
   c->args_y.sweep = 1;
   c->args_y.redo_off = 2 + c->ntx;
+  c->args_y.fold_advance = prec == FVNA_FP32_PERT ? 1 : 0;
 
 
   // initial state
@@ -667,7 +668,7 @@ int fvna_step_timed(fvna_ctx *c, float ms[3]) {
   if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
   if (e == cudaSuccess) e = sweep_y(c, c->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->stream);
-  if (e == cudaSuccess) e = launch_advance(c->args, c->stream);
+  if (e == cudaSuccess && !c->args_y.fold_advance) e = launch_advance(c->args, c->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[3], c->stream);
   if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
@@ -742,7 +743,13 @@ int fvna_set_correction(fvna_ctx *c, fvna_net *net, float in_scale, float out_sc
   CK(cudaStreamSynchronize(c->stream));
   if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
   if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  // the correction runs between the x2 sweep and the step end, so with a
+  // network the step end is its own launch again
   c->kernels_per_step += (net ? 3 : 0) - (c->net ? 3 : 0);
+  if (c->cfg.precision == FVNA_FP32_PERT) {
+    c->kernels_per_step += (net ? 1 : 0) - (c->net ? 1 : 0);
+    c->args_y.fold_advance = net ? 0 : 1;
+  }
   c->net = net;
   c->net_in = in_scale;
   c->net_out = out_scale;

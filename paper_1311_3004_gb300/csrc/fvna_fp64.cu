@@ -6,6 +6,7 @@
 // because it is binary64 for both precisions (section 4: dt from the CFL
 // number of the previous step).
 #include "fvna_launch.h"
+#include "fvna_step.cuh"
 #include "fvna_sweeps.cuh"
 
 #define POLICY P64
@@ -16,68 +17,10 @@
 
 namespace fvna {
 
-// Constants of one step derived from dt, evaluated once per domain and step
-// (dt/dx for the sweeps, dt*delta/dx^2 for the source), in binary64 and
-// rounded to binary32 for the perturbation kernels.
-__device__ __forceinline__ void set_step_scalars(DomScal *S, const StepArgs &A) {
-  S->lam = S->dt / A.dx;
-  S->coef = S->dt * A.delta / (A.dx * A.dx);
-  S->lam32 = (float)S->lam;
-  S->coef32 = (float)S->coef;
-  S->dt32 = (float)S->dt;
-}
-
-// End of a step for every domain: CFL number of the step just taken, the
-// CFL statistics (Welford), dt of the next step (nu_W dx / max|s|), time,
-// budgets, and whether the run goes on.  A step that would pass t_end is
-// shortened to end on it.
+// End of a step for every domain (see fvna_step.cuh).
 __global__ void k_advance(StepArgs A) {
   int d = blockIdx.x * blockDim.x + threadIdx.x;
-  if (d >= A.ndom) return;
-  DomScal *S = A.scal + d;
-  if (S->done) return;
-  double smax = __longlong_as_double((long long)S->smax_bits);
-  int st = 0;
-  if (S->status_bits & ST_NONREAL) st |= ST_NONREAL;
-  if (S->status_bits & ST_TIMEOUT) st |= ST_TIMEOUT;
-  if (smax != smax) st |= ST_NAN;
-  double dt = S->dt;
-  if (A.sweeps & 3) {
-    double nu = dt * smax / A.dx;
-    if (nu > A.nu_max) st |= ST_CFL;
-    if (!S->last) {
-      if (nu < S->nu_min) S->nu_min = nu;
-      if (nu > S->nu_max) S->nu_max = nu;
-      S->nu_count += 1;
-      double dd = nu - S->nu_mean;
-      S->nu_mean += dd / (double)S->nu_count;
-      S->nu_m2 += dd * (nu - S->nu_mean);
-    }
-  }
-  if (A.dt_fixed <= 0.0 && smax > 0.0) S->dt_cfl = A.nu_w * A.dx / smax;
-  S->dt_last = dt;
-  S->smax_last = smax;
-  S->t = S->last ? S->t_end : S->t + dt;
-  S->step += 1;
-  for (int k = 0; k < 3; k++) {
-    S->budget[k] = S->budget_acc[k];
-    S->budget_acc[k] = 0.0;
-  }
-  S->smax_bits = 0ull;
-  S->status_bits = 0;
-  S->status |= st;
-  if (S->steps_left > 0) S->steps_left -= 1;
-  if (S->status != 0 || S->steps_left == 0 || (S->timed && !(S->t < S->t_end))) {
-    S->done = 1;
-    return;
-  }
-  S->dt = S->dt_cfl;
-  S->last = 0;
-  if (S->timed && S->t + S->dt >= S->t_end) {
-    S->dt = S->t_end - S->t;
-    S->last = 1;
-  }
-  set_step_scalars(S, A);
+  if (d < A.ndom) advance_domain(A, d);
 }
 
 // Start of a run: time limit and step budget, dt of the first step.

@@ -22,6 +22,7 @@
 // from the ghost ring (k_ghost32), so the border path stays light.
 #pragma once
 
+#include "fvna_step.cuh"
 #include "fvna_sweeps.cuh"
 #include "fvna_x2.cuh"
 
@@ -749,6 +750,23 @@ __device__ __forceinline__ int y32_tile(const StepArgs &A, const DomDev &D, DomS
 
 }  // namespace x2
 
+// The end of the step in the x2 sweep's second kernel: the last block to
+// finish runs the per-domain step end (fvna_step.cuh) once every tile's
+// statistics are in.
+__device__ __forceinline__ void y32_finish_step(const StepArgs &A, int lane) {
+  if (!A.fold_advance) return;
+  unsigned prev = 0;
+  if (lane == 0) {
+    __threadfence();
+    prev = atomicAdd(&A.counters[2], 1u);
+  }
+  prev = __shfl_sync(0xffffffffu, prev, 0);
+  if (prev != gridDim.x - 1) return;
+  __threadfence();
+  for (int d = lane; d < A.ndom; d += 32) advance_domain(A, d);
+  if (lane == 0) A.counters[2] = 0u;
+}
+
 template <int LIM, bool COMP, bool REDO>
 __global__ void __launch_bounds__(32, Y32_MINBLOCKS) k_sweep_y32(StepArgs A) {
   using namespace x2;
@@ -760,6 +778,7 @@ __global__ void __launch_bounds__(32, Y32_MINBLOCKS) k_sweep_y32(StepArgs A) {
   const int nredo = REDO ? A.redo[1] : 0;
   if (REDO && nredo == 0) {
     if (blockIdx.x == 0 && lane == 0) A.redo[0] = 0;
+    y32_finish_step(A, lane);
     return;
   }
   if (lane == 0)
@@ -794,6 +813,7 @@ __global__ void __launch_bounds__(32, Y32_MINBLOCKS) k_sweep_y32(StepArgs A) {
     if (rc == 1) break;
     it = REDO ? cur + (int)gridDim.x : take_tile_collect(tn);
   }
+  if (REDO) y32_finish_step(A, lane);
 }
 
 // Analytic border values of the current step into the ghost ring (binary64

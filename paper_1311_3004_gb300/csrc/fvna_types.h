@@ -78,6 +78,8 @@ struct StepArgs {
   int *redo;                     // binary32 sweeps: redo counts of the two sweeps, then lists
   int redo_off;                  // offset of this sweep's redo list in redo
   int sweep;                     // 0: x1 sweep, 1: x2 sweep
+  int fold_advance;              // binary32 x2 sweep: its second kernel ends the step
+                                 // (k_advance's work, by the last block; counters[2])
 };
 
 }  // namespace fvna
