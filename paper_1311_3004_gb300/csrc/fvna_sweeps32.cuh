@@ -753,11 +753,11 @@ __device__ __forceinline__ int y32_tile(const StepArgs &A, const DomDev &D, DomS
 // The end of the step in the x2 sweep's second kernel: the last block to
 // finish runs the per-domain step end (fvna_step.cuh) once every tile's
 // statistics are in.
-__device__ __forceinline__ void y32_finish_step(const StepArgs &A, int lane) {
+__device__ __forceinline__ void y32_finish_step(const StepArgs &A, int lane, bool wrote) {
   if (!A.fold_advance) return;
   unsigned prev = 0;
   if (lane == 0) {
-    __threadfence();
+    if (wrote) __threadfence();   // this block's statistics before its arrival
     prev = atomicAdd(&A.counters[2], 1u);
   }
   prev = __shfl_sync(0xffffffffu, prev, 0);
@@ -778,7 +778,7 @@ __global__ void __launch_bounds__(32, Y32_MINBLOCKS) k_sweep_y32(StepArgs A) {
   const int nredo = REDO ? A.redo[1] : 0;
   if (REDO && nredo == 0) {
     if (blockIdx.x == 0 && lane == 0) A.redo[0] = 0;
-    y32_finish_step(A, lane);
+    y32_finish_step(A, lane, false);
     return;
   }
   if (lane == 0)
@@ -813,7 +813,7 @@ __global__ void __launch_bounds__(32, Y32_MINBLOCKS) k_sweep_y32(StepArgs A) {
     if (rc == 1) break;
     it = REDO ? cur + (int)gridDim.x : take_tile_collect(tn);
   }
-  if (REDO) y32_finish_step(A, lane);
+  if (REDO) y32_finish_step(A, lane, true);
 }
 
 // Analytic border values of the current step into the ghost ring (binary64
