@@ -106,6 +106,38 @@ def test_step_parity_fp64(name, case, steps):
     assert sg["nu_mean"] == pytest.approx(so["nu_mean"], rel=1e-14, abs=1e-15)
 
 
+TOL32 = 1e-5   # binary32 perturbation form against the binary64 oracle (perturbation-relative)
+
+
+@pytest.mark.parametrize("name,case,steps", _cases(), ids=[c[0] for c in _cases()])
+def test_step_parity_fp32(name, case, steps):
+    """Every case above through the binary32 kernels (borders, limiters,
+    sweeps switched off, one-row and one-column domains, fixed dt)."""
+    qo, so = run_oracle(case, steps)
+    qg, sg = run_gpu(case, steps, precision=fvna.FP32_PERT)
+    assert so["status"] == 0 and sg["rc"] == 0
+    assert sg["steps"] == so["step"] == steps
+    err = pert_rel_linf(qg, qo)
+    assert err <= TOL32, err
+    assert sg["t"] == pytest.approx(so["t"], rel=1e-6)
+
+
+@pytest.mark.parametrize("tile_x,tile_y,compensated",
+                         [(16, 10, 1), (32, 18, 1), (64, 18, 1), (16, 8, 0), (32, 64, 0),
+                          (64, 34, 1), (64, 8, 0)])
+def test_fp32_tile_shapes(tile_x, tile_y, compensated):
+    """The binary32 sweeps for every x1 tile width (halves of 8, 16, 32 cells:
+    the three TMA swizzle spans), several x2 tile heights (ring chunks full
+    and ragged) and both update forms, against the oracle."""
+    q = wl.random_cells(150, 140, 1e-3, seed=31)
+    c = Case(150, 140, q, bc=(P, P, E, R), delta=2e-3)
+    qo, _ = run_oracle(c, 15)
+    qg, sg = run_gpu(c, 15, precision=fvna.FP32_PERT, tile_x=tile_x, tile_y=tile_y,
+                     compensated=compensated)
+    assert sg["rc"] == 0
+    assert pert_rel_linf(qg, qo) <= TOL32
+
+
 @pytest.mark.parametrize("tile_x,tile_y", [(32, 8), (64, 16), (32, 128), (64, 64), (16, 32)])
 def test_tile_shapes_give_identical_results(tile_x, tile_y):
     q = wl.random_cells(150, 140, 1e-3, seed=31)
