@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=["gaussian", "plane", "focused", "batched", "learned",
-                                           "netfwd"],
+                                           "netfwd", "taylor"],
                     default="gaussian",
                     help="gaussian: the headline line; the others print their own line")
     ap.add_argument("--no-e2e", action="store_true")
@@ -443,6 +443,67 @@ def run_focused(args):
     return 0
 
 
+def run_taylor(args):
+    """The Taylor-shock study of section 4.1 (Table tab:error-ts) in binary64 on
+    windows that follow the shock to t = 100: every angle theta_T in {0,
+    pi/32, pi/16, pi/8, pi/4}, eta in {5, 10, 20, 41, 82}, nu_W in {0.6, 0.7,
+    0.8, 0.9, 0.99}.  Per angle: the convergence rates of E_1 and E_inf over
+    eta (best, worst and mean over nu_W), the worst R^2 of the fits, and the
+    best and worst errors at eta = 82, as the paper's table lists them; plus
+    the cell-updates and the time of the whole study."""
+    torch, fvna = _setup_cuda()
+    from paper_1311_3004_gb300 import analysis
+    ratio, beta, T = 1e-7, 3.5, 100.0
+    etas = [5, 10, 20, 41, 82]
+    nus = [0.6, 0.7, 0.8, 0.9, 0.99]
+    table, cell_updates, total_s = {}, 0.0, 0.0
+    for k in (0, 32, 16, 8, 4):
+        angle = 0.0 if k == 0 else np.pi / k
+        rows = {"E1": [], "Einf": []}
+        for nu in nus:
+            e1s, eis = [], []
+            for eta in etas:
+                dx = 1.0 / eta
+                if k == 0:
+                    nx, ny, x0, y0, bc = int(round(30.0 * eta)), 4, -15.0, 0.0, (3, 3, 0, 0)
+                else:
+                    nx = ny = int(round(12.0 * eta))
+                    x0 = y0 = -6.0
+                    bc = (3, 3, 3, 3)
+                q0 = wl.taylor_initial(nx, ny, dx, ratio, x0=x0, y0=y0, angle=angle)
+                cfg = fvna.make_config(precision=fvna.FP64, beta=beta, delta=ratio * beta, dx=dx,
+                                       nu_w=nu)
+                dom = fvna.make_domain(nx, ny, bc=bc, x0=x0, y0=y0, taylor_ratio=ratio,
+                                       taylor_angle=angle)
+                s = fvna.Solver(cfg, [dom], [q0])
+                st, sec = _timed(torch, lambda: s.run_moving(T, 0.0, (np.cos(angle),
+                                                                      np.sin(angle)), every=32))
+                q, (cx, cy) = s.q(0), s.corner(0)
+                s.close()
+                e1, ei = analysis.taylor_line_errors(q, cx, cy, dx, T, angle, ratio)
+                e1s.append(e1)
+                eis.append(ei)
+                cell_updates += nx * ny * st["steps"]
+                total_s += sec
+            for name, e in (("E1", e1s), ("Einf", eis)):
+                fit = np.polyfit(np.log(etas), np.log(e), 1)
+                pred = np.polyval(fit, np.log(etas))
+                r2 = 1.0 - np.sum((np.log(e) - pred) ** 2) / np.sum(
+                    (np.log(e) - np.mean(np.log(e))) ** 2)
+                rows[name].append((-fit[0], r2, e[-1]))
+        key = "0" if k == 0 else f"pi/{k}"
+        table[key] = {n: {"rate_best": max(r[0] for r in v), "rate_worst": min(r[0] for r in v),
+                          "rate_mean": float(np.mean([r[0] for r in v])),
+                          "worst_r2": min(r[1] for r in v),
+                          "err82_best": min(r[2] for r in v), "err82_worst": max(r[2] for r in v)}
+                      for n, v in rows.items()}
+    print(json.dumps({"metric": METRIC, "value": cell_updates / total_s, "unit": METRIC,
+                      "workload": "taylor_shock_study_moving_window", "dtype": "f64",
+                      "cell_updates": cell_updates, "time_s": total_s, "table": table}),
+          flush=True)
+    return 0
+
+
 def run_batched(args):
     """64 domains of uneven size in one context (one launch per sub-step over
     all of them), FP32, autotuned tiles, 1000 steps each with its own dt;
@@ -582,6 +643,8 @@ def main():
         return run_focused(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "taylor":
+        return run_taylor(args)
     return run_native(args)
 
 

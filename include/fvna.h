@@ -70,7 +70,9 @@ enum fvna_field {
   FVNA_FIELD_Q = 0,         /* 3*nx*ny binary64 total variables */
   FVNA_FIELD_PRESSURE = 1,  /* nx*ny binary64 p'/(rho0 c0^2) = q1 - 1 (linear EOS, section 2) */
   FVNA_FIELD_BUDGET = 2,    /* 3 binary64: sum over cells of (q1-1, q2, q3) after the last step */
-  FVNA_FIELD_STATS = 3      /* one fvna_stats */
+  FVNA_FIELD_STATS = 3,     /* one fvna_stats */
+  FVNA_FIELD_CORNER = 4     /* 2 binary64: the window's lower-left corner (x0, y0), moved by
+                               fvna_shift */
 };
 
 /* ---- configuration ----------------------------------------------------- */
@@ -158,6 +160,36 @@ int fvna_sync(fvna_ctx *ctx);
  * `bytes` bytes (host or device, per dst_on_device); see enum fvna_field for
  * sizes.  Synchronises the stream.  FVNA_ERR_ARG if bytes is too small. */
 int fvna_fields(fvna_ctx *ctx, int domain, int what, void *dst, size_t bytes, int dst_on_device);
+
+/* fvna_shift -- move the window of one domain by (kx, ky) whole cells: the
+ * moving domain of section 4 (in the second stage of a run the domain moves
+ * with the wave).  Afterwards cell (i, j) holds what was cell (i + kx, j + ky)
+ * and the corner (x0, y0) has moved by (kx dx, ky dx).  A cell with no old
+ * counterpart enters through a border and takes what that border's rule
+ * gives at the domain's current time: FVNA_BC_TAYLOR the analytic value of
+ * eq. OurTaylorS at the new cell centre, FVNA_BC_PERIODIC the wrapped old
+ * cell, any other rule the nearest old cell (zero-order extrapolation).  A
+ * cell entering through a corner takes the analytic value if either border
+ * is a Taylor border, else both rules in turn.  Enqueued on the context's
+ * stream after the work already enqueued (asynchronous; errors of the two
+ * kernels surface at the next synchronising call).  Returns FVNA_ERR_ARG for
+ * a NULL context, a bad domain index, |kx| >= nx, |ky| >= ny, or ky != 0 in
+ * the axisymmetric geometry (where x2 is the radius). */
+int fvna_shift(fvna_ctx *ctx, int domain, int kx, int ky);
+
+/* fvna_run_moving -- a two-stage run with a moving domain (section 4): the
+ * window of every domain stays at rest until its time t passes t1, then
+ * follows the wave at velocity (vx, vy) (x1 and x2 units per unit time; for
+ * a plane wave the unit sound speed times its direction).  The run proceeds
+ * in chunks of `every` steps, each taken as by fvna_run(ctx, t_end, every);
+ * after each chunk a domain whose window lags the target displacement
+ * (round(vx (t - t1) / dx), round(vy (t - t1) / dx)) cells, counted from
+ * where the window was when the context was created, is moved by the
+ * difference with fvna_shift.  Stops at t_end, after max_steps steps, or at
+ * the first device error, like fvna_run (same return codes; stats as there).
+ * FVNA_ERR_ARG if every < 1, or for a shift fvna_shift would refuse. */
+int fvna_run_moving(fvna_ctx *ctx, double t_end, long long max_steps, double t1, double vx,
+                    double vy, int every, fvna_stats *stats);
 
 /* fvna_step_timed -- take one step with its kernels launched one by one (not
  * from the step graph), CUDA events recorded between them on the context's

@@ -67,6 +67,9 @@ def lib():
         L.ora_scalars.argtypes = [ctypes.c_void_p, dp]
         L.ora_interface.restype = ctypes.c_int
         L.ora_interface.argtypes = [ctypes.c_double, dp, dp, dp, dp, dp, dp]
+        L.ora_shift.restype = ctypes.c_int
+        L.ora_shift.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+        L.ora_corner.argtypes = [ctypes.c_void_p, dp]
         L.ora_limiter.restype = ctypes.c_double
         L.ora_limiter.argtypes = [ctypes.c_int, ctypes.c_double]
         _lib = L
@@ -127,6 +130,16 @@ class Oracle:
         t_end = float(t_end) if np.isfinite(t_end) else -1e300
         return int(lib().ora_run(self._h, t_end, int(steps)))
 
+    def shift(self, kx: int, ky: int) -> None:
+        """Move the window by (kx, ky) cells (moving domain, see ora_shift)."""
+        if lib().ora_shift(self._h, int(kx), int(ky)) != 0:
+            raise ValueError(f"shift ({kx}, {ky}) out of range")
+
+    def corner(self) -> tuple:
+        out = np.zeros(2, dtype=np.float64)
+        lib().ora_corner(self._h, _dptr(out))
+        return float(out[0]), float(out[1])
+
     def q(self) -> np.ndarray:
         out = np.empty((3, self.params.ny, self.params.nx), dtype=np.float64)
         lib().ora_get(self._h, _dptr(out))
@@ -164,6 +177,36 @@ def interface(beta: float, qL, qR):
 
 def limiter(kind: int, theta: float) -> float:
     return float(lib().ora_limiter(kind, theta))
+
+
+def run_moving(o: Oracle, t_end: float, t1: float, velocity, every: int,
+               max_steps: int = 2 ** 62) -> None:
+    """Two-stage run with a moving window (section 4: the domain is at rest
+    until t1, then moves with the wave).  The run goes in chunks of `every`
+    steps; after each chunk the window is moved by whole cells so that its
+    displacement since the start is (round(v_x (t - t1) / dx), round(v_y (t -
+    t1) / dx)).  Stops at t_end, after max_steps steps, or on a nonzero
+    status."""
+    dx = o.params.dx
+    timed = t_end > o.scalars()["t"]
+    moved = [0, 0]
+    left = int(max_steps)
+    while left > 0:
+        n = min(int(every), left)
+        o.run(n, t_end)
+        left -= n
+        sc = o.scalars()
+        if sc["status"]:
+            break
+        if sc["t"] > t1:
+            e = sc["t"] - t1
+            tx = int(np.floor(velocity[0] * e / dx + 0.5))
+            ty = int(np.floor(velocity[1] * e / dx + 0.5))
+            if tx != moved[0] or ty != moved[1]:
+                o.shift(tx - moved[0], ty - moved[1])
+                moved = [tx, ty]
+        if timed and not sc["t"] < t_end:
+            break
 
 
 def run(params: Params, q0: np.ndarray, steps: int, t_end: float = -np.inf):

@@ -503,6 +503,61 @@ long ora_run(ora_state *st, double t_end, long max_steps) {
   return done;
 }
 
+/* Moving domain (section 4: in the second stage of a run the domain moves
+ * with the wave).  The window moves by (kx, ky) whole cells: afterwards cell
+ * (i, j) holds what was cell (i + kx, j + ky), and the lower-left corner
+ * moved by (kx dx, ky dx).  A cell with no old counterpart comes in through
+ * a border and takes what that border's rule gives at the current time t:
+ * the Taylor shock its analytic value (eq. OurTaylorS) at the new cell
+ * centre; periodic the wrapped old cell; every other rule the nearest old
+ * cell (zero-order extrapolation).  A cell coming in through a corner takes
+ * the analytic value if either border is a Taylor border, else both rules in
+ * turn.  Returns 0, or -1 when |kx| >= nx or |ky| >= ny. */
+int ora_shift(ora_state *st, int kx, int ky) {
+  ora_params *p = &st->p;
+  int nx = p->nx, ny = p->ny;
+  if (kx <= -nx || kx >= nx || ky <= -ny || ky >= ny) return -1;
+  double x0n = p->x0 + kx * p->dx;
+  double y0n = p->y0 + ky * p->dx;
+  size_t n = (size_t)nx * (size_t)ny;
+  double *nq = malloc(sizeof(double) * 3 * n);
+  for (int j = 0; j < ny; j++) {
+    for (int i = 0; i < nx; i++) {
+      int si = i + kx, sj = j + ky;
+      int out_x = si < 0 || si >= nx, out_y = sj < 0 || sj >= ny;
+      int bx = p->bc[si < 0 ? 0 : 1], by = p->bc[sj < 0 ? 2 : 3];
+      double v[3];
+      if ((out_x && bx == BC_TAYLOR) || (out_y && by == BC_TAYLOR)) {
+        taylor_value(p, x0n + (i + 0.5) * p->dx, y0n + (j + 0.5) * p->dx, st->t, v);
+      } else {
+        if (out_x) {
+          if (bx == BC_PERIODIC) si = si < 0 ? si + nx : si - nx;
+          else si = si < 0 ? 0 : nx - 1;
+        }
+        if (out_y) {
+          if (by == BC_PERIODIC) sj = sj < 0 ? sj + ny : sj - ny;
+          else sj = sj < 0 ? 0 : ny - 1;
+        }
+        for (int k = 0; k < 3; k++) v[k] = st->q[k][idx(st, si, sj)];
+      }
+      for (int k = 0; k < 3; k++) nq[(size_t)k * n + (size_t)j * nx + i] = v[k];
+    }
+  }
+  for (int k = 0; k < 3; k++)
+    for (int j = 0; j < ny; j++)
+      for (int i = 0; i < nx; i++) st->q[k][idx(st, i, j)] = nq[(size_t)k * n + (size_t)j * nx + i];
+  free(nq);
+  p->x0 = x0n;
+  p->y0 = y0n;
+  return 0;
+}
+
+/* Lower-left corner of the window: out[0] = x0, out[1] = y0. */
+void ora_corner(const ora_state *st, double *out) {
+  out[0] = st->p.x0;
+  out[1] = st->p.y0;
+}
+
 /* Copy the domain cells out: q[k*nx*ny + j*nx + i]. */
 void ora_get(const ora_state *st, double *q) {
   int nx = st->p.nx, ny = st->p.ny;

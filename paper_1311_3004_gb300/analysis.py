@@ -1,0 +1,54 @@
+"""Post-processing of solver output: the error measures of section 4.1.
+
+The Taylor-shock errors of eq. error compare the numerical q1 - 1 with the
+analytic profile of eq. OurTaylorS, -(dt~/beta) tanh(x . n - t), on a 10-unit
+line along the propagation direction n = (cos theta_T, sin theta_T), centred on
+the shock: E_1 = |num - ref|_1 / |ref|_1 and E_inf = |num - ref|_inf /
+|ref|_inf.  The line is sampled at cell centres when it runs along a grid row
+(theta_T = 0) and bilinearly otherwise.  This is host-side evaluation of a
+result (numpy), not part of the scheme.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def taylor_line_errors(q: np.ndarray, x0: float, y0: float, dx: float, t: float, angle: float,
+                       ratio: float, half: float = 5.0, samples: int = 401):
+    """(E_1, E_inf) of the state q (3, ny, nx; total variables) of a window with
+    lower-left corner (x0, y0), at time t.  The line passes through the point of
+    the shock (x . n = t) nearest to the window centre."""
+    ny, nx = q.shape[1:]
+    ct, st = math.cos(angle), math.sin(angle)
+    f = q[0] - 1.0
+    if angle == 0.0:
+        x = x0 + (np.arange(nx) + 0.5) * dx
+        row = ny // 2
+        sel = np.abs(x - t) <= half
+        num = f[row, sel]
+        ref = -ratio * np.tanh(x[sel] - t)
+    else:
+        cx, cy = x0 + 0.5 * nx * dx, y0 + 0.5 * ny * dx
+        s0 = cx * ct + cy * st
+        cx, cy = cx + (t - s0) * ct, cy + (t - s0) * st
+        s = np.linspace(-half, half, samples)
+        px, py = cx + s * ct, cy + s * st
+        fi, fj = (px - x0) / dx - 0.5, (py - y0) / dx - 0.5
+        i0, j0 = np.floor(fi).astype(int), np.floor(fj).astype(int)
+        if i0.min() < 0 or j0.min() < 0 or i0.max() + 1 >= nx or j0.max() + 1 >= ny:
+            raise ValueError("the error line leaves the window")
+        a, b = fi - i0, fj - j0
+        num = ((1 - a) * (1 - b) * f[j0, i0] + a * (1 - b) * f[j0, i0 + 1]
+               + (1 - a) * b * f[j0 + 1, i0] + a * b * f[j0 + 1, i0 + 1])
+        ref = -ratio * np.tanh(s)
+    e1 = float(np.sum(np.abs(num - ref)) / np.sum(np.abs(ref)))
+    einf = float(np.max(np.abs(num - ref)) / np.max(np.abs(ref)))
+    return e1, einf
+
+
+def convergence_rate(etas, errors) -> float:
+    """Slope of the linear regression of log(E) on log(eta), negated (section 4.1)."""
+    return float(-np.polyfit(np.log(np.asarray(etas, float)), np.log(np.asarray(errors, float)),
+                             1)[0])

@@ -1,10 +1,9 @@
 """Build the in-tree CUDA library libfvna.so for sm_103a.
 
-Three translation units are compiled in parallel with nvcc and linked with
+The translation units are compiled in parallel with nvcc and linked with
 the static CUDA runtime:
   fvna_fp64.cu  binary64 kernels, -fmad=false (products never fused into sums)
   fvna_fp32.cu  binary32 perturbation kernels
-  fvna_fp32_redo.cu  the binary32 sweeps' second kernels (general split)
   fvna_api.cu   host runtime behind include/fvna.h
   fvna_noalloc.cu  the allocation-free binary64 step (fixed device scratch array)
   fvna_net.cu   the learned correction (BF16 tensor-core forward, FP32 backward)
@@ -26,7 +25,6 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 UNITS = {
     "fvna_fp64": ["-fmad=false"],
     "fvna_fp32": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
-    "fvna_fp32_redo": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "fvna_api": [],
     "fvna_noalloc": ["-fmad=false"],
     "fvna_net": [],

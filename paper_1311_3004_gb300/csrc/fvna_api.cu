@@ -55,9 +55,11 @@ struct fvna_ctx {
   __nv_bfloat16 *net_h = nullptr;   // two hidden activation buffers
   void *d_maps = nullptr;           // binary32: TMA tensor maps of every domain
   unsigned *d_ctr = nullptr;        // binary32: tile counters of the two sweeps
-  int *d_redo = nullptr;            // binary32: redo counts and lists of the two sweeps
+  int *d_redo = nullptr;            // binary32: x2-sweep tiles listed for the general split
   int redo_blocks = 1;
   double *d_budget = nullptr;       // binary32: on-demand budget sums
+  // moving domain: whole cells each window has moved since init (x1, x2)
+  std::vector<long long> moved_x, moved_y;
 };
 
 namespace {
@@ -150,13 +152,12 @@ int enqueue_drives(fvna_ctx *c, cudaStream_t s) {
   return FVNA_OK;
 }
 
-// a sweep: binary64 one kernel; binary32 the speculative kernel, then the
-// kernel that redoes the tiles it listed (usually none)
+// a sweep: binary64 one kernel; binary32 x1 one kernel (a tile that meets a
+// face that is not subsonic is redone inside it), binary32 x2 the
+// speculative kernel, then the kernel that redoes the tiles it listed
+// (usually none: it returns at once)
 cudaError_t sweep_x(fvna_ctx *c, cudaStream_t s) {
-  cudaError_t e = launch_sweep_x(c->cfg.precision, c->tile_x, c->args_x, c->blocks_x, s);
-  if (e == cudaSuccess && c->cfg.precision == FVNA_FP32_PERT)
-    e = launch_sweep_x_redo32(c->tile_x, c->args_x, c->redo_blocks, s);
-  return e;
+  return launch_sweep_x(c->cfg.precision, c->tile_x, c->args_x, c->blocks_x, s);
 }
 cudaError_t sweep_y(fvna_ctx *c, cudaStream_t s) {
   cudaError_t e = launch_sweep_y(c->cfg.precision, c->args_y, c->blocks_y, s);
@@ -274,6 +275,11 @@ cudaError_t launch_import(int p, const DomDev &d, const double *q0, cudaStream_t
 cudaError_t launch_export(int p, const DomDev &d, double *out, int what, cudaStream_t s) {
   return p == FVNA_FP64 ? launch_export_fp64(d, out, what, s) : launch_export_fp32(d, out, what, s);
 }
+cudaError_t launch_shift(int p, const DomDev &d, DomDev *dd, int dom, const DomScal *scal, int kx,
+                         int ky, double dx, cudaStream_t s) {
+  return p == FVNA_FP64 ? launch_shift_fp64(d, dd, dom, scal, kx, ky, dx, s)
+                        : launch_shift_fp32(d, dd, dom, scal, kx, ky, dx, s);
+}
 cudaError_t launch_riemann(int p, double beta, int n, const double *qL, const double *qR, double *s,
                            double *W, double *am, double *ap, int *nr, cudaStream_t st) {
   return p == FVNA_FP64 ? launch_riemann_fp64(beta, n, qL, qR, s, W, am, ap, nr, st)
@@ -390,6 +396,8 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   }
   CK(cudaMalloc(&c->d_state, total));
   c->dd.resize(n);
+  c->moved_x.assign(n, 0);
+  c->moved_y.assign(n, 0);
   for (int d = 0; d < n; d++) {
     const fvna_domain &D = doms[d];
     DomDev &g = c->dd[d];
@@ -472,11 +480,10 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
     CK(cudaMalloc(&c->d_budget, 3 * sizeof(double)));
     CK(cudaMalloc(&c->d_ctr, 3 * sizeof(unsigned)));
     CK(cudaMemsetAsync(c->d_ctr, 0, 3 * sizeof(unsigned), c->stream));
-    CK(cudaMalloc(&c->d_redo, (2 + (size_t)c->ntx + c->nty) * sizeof(int)));
+    CK(cudaMalloc(&c->d_redo, (2 + (size_t)c->nty) * sizeof(int)));
     CK(cudaMemsetAsync(c->d_redo, 0, 2 * sizeof(int), c->stream));
-    CK(prepare_kernels_redo32(c->tile_x, cfg->limiter, comp));
     c->redo_blocks = sms;
-    c->kernels_per_step += 1;   // two second kernels; the step end runs in one of them
+    // x1 sweep, x2 sweep and its second kernel, which ends the step
   }
 
   StepArgs &a = c->args;
@@ -496,12 +503,11 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   c->args_x.tiles = c->d_tx;
   c->args_x.ntiles = c->ntx;
   c->args_x.sweep = 0;
-  c->args_x.redo_off = 2;
   c->args_y = a;
   c->args_y.tiles = c->d_ty;
   c->args_y.ntiles = c->nty;
+  c->args_y.redo_off = 2;
   c->args_y.sweep = 1;
-  c->args_y.redo_off = 2 + c->ntx;
   c->args_y.fold_advance = prec == FVNA_FP32_PERT ? 1 : 0;
 
 
@@ -586,6 +592,57 @@ int fvna_run(fvna_ctx *c, double t_end, long long max_steps, fvna_stats *stats) 
   return first_status(c);
 }
 
+int fvna_shift(fvna_ctx *c, int domain, int kx, int ky) {
+  if (!c || domain < 0 || domain >= c->ndom) return FVNA_ERR_ARG;
+  const fvna_domain &D = c->doms[domain];
+  if (kx <= -D.nx || kx >= D.nx || ky <= -D.ny || ky >= D.ny) return FVNA_ERR_ARG;
+  if (ky != 0 && c->cfg.geometry == FVNA_AXISYMMETRIC) return FVNA_ERR_ARG;
+  if (kx == 0 && ky == 0) return FVNA_OK;
+  CK(launch_shift(c->cfg.precision, c->dd[domain], c->d_dd, domain, c->d_scal, kx, ky, c->cfg.dx,
+                  c->stream));
+  c->launches += 2;
+  c->moved_x[domain] += kx;
+  c->moved_y[domain] += ky;
+  return FVNA_OK;
+}
+
+int fvna_run_moving(fvna_ctx *c, double t_end, long long max_steps, double t1, double vx,
+                    double vy, int every, fvna_stats *stats) {
+  if (!c || max_steps < 0 || every < 1) return FVNA_ERR_ARG;
+  int rc = read_scal(c);
+  if (rc != FVNA_OK) return rc;
+  // a time limit ends the run once a domain reaches it (a later chunk would
+  // no longer be limited by it)
+  std::vector<char> timed(c->ndom);
+  for (int d = 0; d < c->ndom; d++) timed[d] = t_end > c->h_scal[d].t;
+  long long left = max_steps;
+  while (left > 0) {
+    const long long n = std::min<long long>(every, left);
+    rc = fvna_run(c, t_end, n, nullptr);
+    if (rc != FVNA_OK) break;
+    left -= n;
+    // h_scal holds every domain's scalars after the chunk
+    bool reached = false;
+    for (int d = 0; d < c->ndom; d++) {
+      const DomScal &S = c->h_scal[d];
+      reached |= timed[d] && !(S.t < t_end);
+      if (!(S.t > t1)) continue;
+      const double e = S.t - t1;
+      const long long tx = (long long)std::floor(vx * e / c->cfg.dx + 0.5);
+      const long long ty = (long long)std::floor(vy * e / c->cfg.dx + 0.5);
+      const long long kx = tx - c->moved_x[d], ky = ty - c->moved_y[d];
+      if (kx == 0 && ky == 0) continue;
+      rc = fvna_shift(c, d, (int)kx, (int)ky);
+      if (rc != FVNA_OK) break;
+    }
+    if (rc != FVNA_OK || reached) break;
+  }
+  if (rc == FVNA_OK) rc = read_scal(c);
+  if (rc != FVNA_OK) return rc;
+  if (stats) fill_stats(c->h_scal[0], stats);
+  return first_status(c);
+}
+
 int fvna_sync(fvna_ctx *c) {
   if (!c) return FVNA_ERR_ARG;
   int rc = read_scal(c);
@@ -618,6 +675,17 @@ int fvna_fields(fvna_ctx *c, int domain, int what, void *dst, size_t bytes, int 
       CK(cudaMemcpyAsync(dst, c->d_stage, need, cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
     }
+    return FVNA_OK;
+  }
+  if (what == FVNA_FIELD_CORNER) {
+    // the device descriptor holds the corner (fvna_shift moves it there)
+    if (bytes < 2 * sizeof(double)) return FVNA_ERR_ARG;
+    DomDev g;
+    CK(cudaMemcpyAsync(&g, c->d_dd + domain, sizeof g, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double xy[2] = {g.x0, g.y0};
+    if (dst_on_device) CK(cudaMemcpy(dst, xy, sizeof xy, cudaMemcpyHostToDevice));
+    else std::memcpy(dst, xy, sizeof xy);
     return FVNA_OK;
   }
   int rc = read_scal(c);

@@ -12,34 +12,23 @@
 #include "fvna_launch.h"
 #include "fvna_sweeps32.cuh"
 
-#ifndef FVNA_REDO
-#define FVNA_REDO_UNIT 0
-#define FVNA_CHECK_SYMBOL fvna_check_word_main
-// this unit: the first kernel of each binary32 sweep and the rest of the
-// binary32 policy; fvna_fp32_redo.cu builds the second kernels from the
-// same source with FVNA_REDO = true
-#define FVNA_REDO false
 #define POLICY P32
 #define SUFFIX fp32
 #define HAS_COMP 1
 #define FVNA_PRECISION_SWEEPS 0
 #include "fvna_precision.inc"
-#endif
 
 namespace fvna {
 
-#if !FVNA_REDO_UNIT
 // tile_x 16 / 32 / 64 -> halves of 8 / 16 / 32 cells (swizzle span 32 / 64 / 128 B)
 int x32_half(int tile_x) { return tile_x == 16 ? 8 : tile_x == 32 ? 16 : 32; }
-
-#endif
 
 namespace {
 
 typedef void (*StepKernel)(StepArgs);
 
 template <int SW, int LIM> StepKernel px_c(bool comp) {
-  return comp ? k_sweep_x32<SW, LIM, true, FVNA_REDO> : k_sweep_x32<SW, LIM, false, FVNA_REDO>;
+  return comp ? k_sweep_x32<SW, LIM, true> : k_sweep_x32<SW, LIM, false>;
 }
 template <int SW> StepKernel px_l(int lim, bool comp) {
   if (lim == LIM_NONE) return px_c<SW, LIM_NONE>(comp);
@@ -52,16 +41,15 @@ StepKernel px(int tile_x, int lim, bool comp) {
   if (sw == 16) return px_l<16>(lim, comp);
   return px_l<32>(lim, comp);
 }
-template <int LIM> StepKernel py_c(bool comp) {
-  return comp ? k_sweep_y32<LIM, true, FVNA_REDO> : k_sweep_y32<LIM, false, FVNA_REDO>;
+template <int LIM, bool REDO> StepKernel py_c(bool comp) {
+  return comp ? k_sweep_y32<LIM, true, REDO> : k_sweep_y32<LIM, false, REDO>;
 }
-StepKernel py(int lim, bool comp) {
-  if (lim == LIM_NONE) return py_c<LIM_NONE>(comp);
-  if (lim == LIM_LW) return py_c<LIM_LW>(comp);
-  return py_c<LIM_MC>(comp);
+template <bool REDO> StepKernel py(int lim, bool comp) {
+  if (lim == LIM_NONE) return py_c<LIM_NONE, REDO>(comp);
+  if (lim == LIM_LW) return py_c<LIM_LW, REDO>(comp);
+  return py_c<LIM_MC, REDO>(comp);
 }
 
-#if !FVNA_REDO_UNIT
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -112,33 +100,17 @@ __global__ void k_budget32(DomDev D, double *dst) {
   }
 }
 
-#endif
 }  // namespace
 
-#if FVNA_REDO_UNIT
-cudaError_t prepare_kernels_redo32(int tile_x, int lim, int comp) {
-  cudaError_t e = cudaFuncSetAttribute(px(tile_x, lim, comp != 0),
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       x32_smem_bytes(x32_half(tile_x)));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(py(lim, comp != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              y32_smem_bytes());
-}
-cudaError_t launch_sweep_x_redo32(int tile_x, const StepArgs &a, int blocks, cudaStream_t s) {
-  px(tile_x, a.limiter, a.compensated != 0)<<<blocks, 32, x32_smem_bytes(x32_half(tile_x)), s>>>(a);
-  return cudaGetLastError();
-}
-cudaError_t launch_sweep_y_redo32(const StepArgs &a, int blocks, cudaStream_t s) {
-  py(a.limiter, a.compensated != 0)<<<blocks, 32, y32_smem_bytes(), s>>>(a);
-  return cudaGetLastError();
-}
-#else
 cudaError_t prepare_kernels_fp32(int tile_x, int lim, int comp) {
   cudaError_t e = cudaFuncSetAttribute(px(tile_x, lim, comp != 0),
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        x32_smem_bytes(x32_half(tile_x)));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(py(lim, comp != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(py<false>(lim, comp != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           y32_smem_bytes());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(py<true>(lim, comp != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
                               y32_smem_bytes());
 }
 
@@ -150,7 +122,8 @@ int occupancy_x_fp32(int tile_x, int lim, int comp) {
 }
 int occupancy_y_fp32(int lim, int comp) {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, py(lim, comp != 0), 32, y32_smem_bytes());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, py<false>(lim, comp != 0), 32,
+                                                y32_smem_bytes());
   return n;
 }
 
@@ -159,7 +132,11 @@ cudaError_t launch_sweep_x_fp32(int tile_x, const StepArgs &a, int blocks, cudaS
   return cudaGetLastError();
 }
 cudaError_t launch_sweep_y_fp32(const StepArgs &a, int blocks, cudaStream_t s) {
-  py(a.limiter, a.compensated != 0)<<<blocks, 32, y32_smem_bytes(), s>>>(a);
+  py<false>(a.limiter, a.compensated != 0)<<<blocks, 32, y32_smem_bytes(), s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_sweep_y_redo32(const StepArgs &a, int blocks, cudaStream_t s) {
+  py<true>(a.limiter, a.compensated != 0)<<<blocks, 32, y32_smem_bytes(), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -215,9 +192,8 @@ cudaError_t launch_budget_fp32(const DomDev &d, double *dst, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-#endif
 }  // namespace fvna
 
 #if FVNA_CHECK
-extern "C" unsigned long long FVNA_CHECK_SYMBOL() { return fvna::check_word_host(); }
+extern "C" unsigned long long fvna_check_word() { return fvna::check_word_host(); }
 #endif

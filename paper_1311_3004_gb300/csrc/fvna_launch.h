@@ -31,6 +31,14 @@ cudaError_t launch_drive_fp32(const StepArgs &a, int dom, int ny, int always, cu
 cudaError_t launch_first_dt(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_import(int precision, const DomDev &d, const double *q0, cudaStream_t s);
 cudaError_t launch_export(int precision, const DomDev &d, double *out, int what, cudaStream_t s);
+// moving domain: shift the window of domain dom by (kx, ky) cells (two
+// kernels on s; the device descriptor's corner moves with it)
+cudaError_t launch_shift(int precision, const DomDev &d, DomDev *dd, int dom, const DomScal *scal,
+                         int kx, int ky, double dx, cudaStream_t s);
+cudaError_t launch_shift_fp64(const DomDev &d, DomDev *dd, int dom, const DomScal *scal, int kx,
+                              int ky, double dx, cudaStream_t s);
+cudaError_t launch_shift_fp32(const DomDev &d, DomDev *dd, int dom, const DomScal *scal, int kx,
+                              int ky, double dx, cudaStream_t s);
 cudaError_t launch_riemann(int precision, double beta, int n, const double *qL, const double *qR,
                            double *s, double *W, double *am, double *ap, int *nonreal,
                            cudaStream_t st);
@@ -66,9 +74,7 @@ int x32_half(int tile_x);
 constexpr int Y32_COLS = 60;
 cudaError_t build_maps_fp32(const DomDev *dd, int n, int tile_x, void **d_maps, cudaStream_t s);
 cudaError_t launch_budget_fp32(const DomDev &d, double *dst, cudaStream_t s);
-// second kernels of the binary32 sweeps (tiles listed for the general split)
-cudaError_t prepare_kernels_redo32(int tile_x, int lim, int comp);
-cudaError_t launch_sweep_x_redo32(int tile_x, const StepArgs &a, int blocks, cudaStream_t s);
+// second kernel of the binary32 x2 sweep (tiles listed for the general split)
 cudaError_t launch_sweep_y_redo32(const StepArgs &a, int blocks, cudaStream_t s);
 // ghost ring of a binary32 domain with a driven border (bytes), and the
 // kernel that fills it with the analytic border values of the current step

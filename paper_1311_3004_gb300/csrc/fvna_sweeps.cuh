@@ -728,6 +728,67 @@ __global__ void k_export(DomDev D, double *out, int what) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Moving domain (section 4: in the second stage of a run the domain moves
+// with the wave).  The window moves by (kx, ky) whole cells: new cell (i, j)
+// takes old cell (i + kx, j + ky).  A cell with no old counterpart comes in
+// through a border and takes what that border's rule gives at the domain's
+// current time: the Taylor shock its analytic value (eq. OurTaylorS) at the
+// new cell centre; periodic the wrapped old cell; every other rule the
+// nearest old cell.  Through a corner: the analytic value if either border
+// is a Taylor border, else both rules in turn.  k_shift writes the moved
+// state into the swept planes; k_shift_back copies it back and moves the
+// corner of the device descriptor (the corner is only ever read from there).
+// Coordinates are rounded operation by operation, so both precisions' units
+// compute the same centres.
+// ---------------------------------------------------------------------------
+template <class P>
+__global__ void k_shift(DomDev D, const DomDev *dd, int dom, const DomScal *S, int kx, int ky,
+                        double dx) {
+  typedef typename P::T T;
+  const int nx = D.nx, ny = D.ny;
+  const double t = S->t;
+  D.x0 = dd[dom].x0;
+  D.y0 = dd[dom].y0;
+  const double x0n = __dadd_rn(D.x0, __dmul_rn((double)kx, dx));
+  const double y0n = __dadd_rn(D.y0, __dmul_rn((double)ky, dx));
+  const long long n = (long long)nx * ny;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(c / nx), i = (int)(c - (long long)j * nx);
+    const size_t off = (size_t)j * D.pitch + i;
+    int si = i + kx, sj = j + ky;
+    const bool ox = si < 0 || si >= nx, oy = sj < 0 || sj >= ny;
+    const int bx = D.bc[si < 0 ? 0 : 1], by = D.bc[sj < 0 ? 2 : 3];
+    if ((ox && bx == BC_TAYLOR) || (oy && by == BC_TAYLOR)) {
+      double v[3];
+      P::taylor(D, __dadd_rn(x0n, __dmul_rn((double)i + 0.5, dx)),
+                __dadd_rn(y0n, __dmul_rn((double)j + 0.5, dx)), t, v);
+      for (int k = 0; k < 3; k++) ((T *)D.qb[k])[off] = (T)v[k];
+      continue;
+    }
+    if (ox) si = bx == BC_PERIODIC ? (si < 0 ? si + nx : si - nx) : (si < 0 ? 0 : nx - 1);
+    if (oy) sj = by == BC_PERIODIC ? (sj < 0 ? sj + ny : sj - ny) : (sj < 0 ? 0 : ny - 1);
+    const size_t so = (size_t)sj * D.pitch + si;
+    for (int k = 0; k < 3; k++) ((T *)D.qb[k])[off] = ((const T *)D.qa[k])[so];
+  }
+}
+template <class P>
+__global__ void k_shift_back(DomDev D, DomDev *dd, int dom, int kx, int ky, double dx) {
+  typedef typename P::T T;
+  const long long n = (long long)D.nx * D.ny;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(c / D.nx), i = (int)(c - (long long)j * D.nx);
+    const size_t off = (size_t)j * D.pitch + i;
+    for (int k = 0; k < 3; k++) ((T *)D.qa[k])[off] = ((const T *)D.qb[k])[off];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    dd[dom].x0 = __dadd_rn(dd[dom].x0, __dmul_rn((double)kx, dx));
+    dd[dom].y0 = __dadd_rn(dd[dom].y0, __dmul_rn((double)ky, dx));
+  }
+}
+
 // Device Roe solver on host-supplied pairs (binary64 total variables in).
 template <class P>
 __global__ void k_riemann(double beta, int n, const double *qL, const double *qR, double *s,

@@ -11,11 +11,14 @@
 //   k_sweep_y32  x2 sweep fused with the source sub-step.  One warp owns 60
 //                columns and tile_y rows; each lane marches two adjacent
 //                columns as a pair (one 8-byte shared-memory read per field
-//                and row).  Rows arrive in chunks of 8 through a TMA ring of
-//                three stages; the source is applied one row behind the
+//                and row).  Rows arrive in chunks of 8 through a two-stage TMA
+//                ring; the source is applied one row behind the
 //                sweep, with the x1 neighbours taken from the adjacent lanes
 //                by shuffles, and the result is stored with coalesced 8-byte
 //                stores.
+// Both sweeps take every face as subsonic (no per-face branch); a tile that
+// met another face is marched again with the general split: at once by the
+// same warp in the x1 sweep, by a second kernel in the x2 sweep.
 // Interior tiles run without any border logic; tiles that touch a domain
 // border (or a ragged edge) take the same code with per-cell border rules
 // and per-face accounting masks.  Analytic border values come precomputed
@@ -371,9 +374,11 @@ __device__ __forceinline__ bool x32_tile(const StepArgs &A, const DomDev &D, Dom
 
 }  // namespace x2
 
-// REDO: the second kernel of the sweep, which marches the tiles the first
-// one listed (a face that was not subsonic) with the general split.
-template <int SW, int LIM, bool COMP, bool REDO>
+// A tile whose speculative march met a face that is not subsonic is loaded
+// again and marched with the general split by the same warp, before its
+// store: its result depends only on the state planes, which no warp of the
+// sweep writes.
+template <int SW, int LIM, bool COMP>
 __global__ void __launch_bounds__(32, X32_MINBLOCKS) k_sweep_x32(StepArgs A) {
   using namespace x2;
   constexpr int BOX = X32_ROWS * SW * 4;
@@ -385,44 +390,41 @@ __global__ void __launch_bounds__(32, X32_MINBLOCKS) k_sweep_x32(StepArgs A) {
   uint64_t *bar = (uint64_t *)(halo + 6 * HB);
   const int lane = threadIdx.x;
   const Maps *maps = (const Maps *)A.tmaps;
-  const int nredo = REDO ? A.redo[0] : 0;
-  if (REDO && nredo == 0) {
-    if (blockIdx.x == 0 && lane == 0) A.redo[1] = 0;
-    return;
-  }
   if (lane == 0) mbar_init(bar, 1);
   if (blockIdx.x == 0 && lane == 0) {
-    if (REDO) A.redo[1] = 0;      // the x2 sweep's list, empty for this step
-    else A.counters[1] = 0u;      // the x2 sweep's tile counter
+    A.counters[1] = 0u;         // the x2 sweep's tile counter
+    A.redo[1] = 0;              // the x2 sweep's list, empty for this step
   }
   __syncwarp();
   unsigned phase = 0;
   const bool xsweep = (A.sweeps & 1) != 0;
-  const int nt = REDO ? nredo : A.ntiles;
-  int it = REDO ? (int)blockIdx.x : take_tile(&A.counters[0], lane);
+  const int nt = A.ntiles;
+  // the tile's boxes: two swizzled halves and the halo columns on both sides
+  auto load = [&](const Maps &M, int x0, int y0) {
+    mbar_expect_tx(bar, 6 * BOX + 6 * HB);
+    for (int f = 0; f < 3; f++) {
+      tma_load(mainb + 2 * f * BOX, &M.xin[f], x0, y0, bar);
+      tma_load(mainb + (2 * f + 1) * BOX, &M.xin[f], x0 + SW, y0, bar);
+      tma_load(halo + 2 * f * HB, &M.xhalo[f], x0 - 4, y0, bar);
+      tma_load(halo + (2 * f + 1) * HB, &M.xhalo[f], x0 + 2 * SW, y0, bar);
+    }
+  };
+  int it = take_tile(&A.counters[0], lane);
+  Tile tl = it < nt ? A.tiles[it] : Tile{0, 0, 0, 0};
   while (it < nt) {
-    const unsigned tn = REDO ? 0u : take_tile_issue(&A.counters[0], lane);
-    const int w = REDO ? A.redo[A.redo_off + it] : it;
-    const int cur = it;
-    const Tile tl = A.tiles[w];
+    const unsigned tn = take_tile_issue(&A.counters[0], lane);
     const DomDev &D = A.doms[tl.dom];
     DomScal *S = A.scal + tl.dom;
-    it = 0;  // set from tn at the end of the body
     if (S->done) {
-      it = REDO ? cur + (int)gridDim.x : take_tile_collect(tn);
+      it = take_tile_collect(tn);
+      if (it < nt) tl = A.tiles[it];
       continue;
     }
     const Maps &M = maps[tl.dom];
     const int x0 = tl.x0, y0 = tl.y0;
     if (lane == 0) {
       bulk_wait_read();  // the previous tile's stores have read the buffers
-      mbar_expect_tx(bar, 6 * BOX + 6 * HB);
-      for (int f = 0; f < 3; f++) {
-        tma_load(mainb + 2 * f * BOX, &M.xin[f], x0, y0, bar);
-        tma_load(mainb + (2 * f + 1) * BOX, &M.xin[f], x0 + SW, y0, bar);
-        tma_load(halo + 2 * f * HB, &M.xhalo[f], x0 - 4, y0, bar);
-        tma_load(halo + (2 * f + 1) * HB, &M.xhalo[f], x0 + 2 * SW, y0, bar);
-      }
+      load(M, x0, y0);
     }
     bool ok = __all_sync(0xffffffffu, mbar_wait(bar, phase));
     if (!ok) {
@@ -430,24 +432,27 @@ __global__ void __launch_bounds__(32, X32_MINBLOCKS) k_sweep_x32(StepArgs A) {
       break;
     }
     phase ^= 1;
-    bool store = true;
-    it = REDO ? cur + (int)gridDim.x : take_tile_collect(tn);
+    it = take_tile_collect(tn);
+    if (it < nt) tl = A.tiles[it];
     if (xsweep) {
-      if (REDO) {
-        x2::x32_tile<SW, LIM, COMP, true, false>(A, D, S, mainb, halo, x0, y0, lane);
-      } else {
-        bool sub = (x0 == 0 || x0 + 2 * SW + 2 > D.nx || y0 + X32_ROWS > D.ny)
-                       ? x2::x32_tile<SW, LIM, COMP, true, true>(A, D, S, mainb, halo, x0, y0, lane)
-                       : x2::x32_tile<SW, LIM, COMP, false, true>(A, D, S, mainb, halo, x0, y0,
-                                                                  lane);
-        if (!sub) {  // left to the second kernel
-          store = false;
-          if (lane == 0) A.redo[A.redo_off + atomicAdd(&A.redo[0], 1)] = w;
+      bool sub = (x0 == 0 || x0 + 2 * SW + 2 > D.nx || y0 + X32_ROWS > D.ny)
+                     ? x2::x32_tile<SW, LIM, COMP, true, true>(A, D, S, mainb, halo, x0, y0, lane)
+                     : x2::x32_tile<SW, LIM, COMP, false, true>(A, D, S, mainb, halo, x0, y0,
+                                                                lane);
+      if (!sub) {
+        // the march wrote into the tile: load it again, general split
+        __syncwarp();
+        if (lane == 0) load(M, x0, y0);
+        if (!__all_sync(0xffffffffu, mbar_wait(bar, phase))) {
+          wait_failed(S, bar, phase, lane);
+          break;
         }
+        phase ^= 1;
+        x2::x32_tile<SW, LIM, COMP, true, false>(A, D, S, mainb, halo, x0, y0, lane);
       }
     }
     __syncwarp();
-    if (store && lane == 0) {
+    if (lane == 0) {
       for (int f = 0; f < 3; f++) {
         tma_store(&M.xout[f], x0, y0, mainb + 2 * f * BOX);
         tma_store(&M.xout[f], x0 + SW, y0, mainb + (2 * f + 1) * BOX);

@@ -75,11 +75,12 @@ struct StepArgs {
   int pad_;
   const void *tmaps;             // binary32 sweeps: TMA tensor maps, one set per domain
   unsigned *counters;            // binary32 sweeps: next-tile counters of the x1 and x2 sweeps
-  int *redo;                     // binary32 sweeps: redo counts of the two sweeps, then lists
-  int redo_off;                  // offset of this sweep's redo list in redo
   int sweep;                     // 0: x1 sweep, 1: x2 sweep
-  int fold_advance;              // binary32 x2 sweep: its second kernel ends the step
-                                 // (k_advance's work, by the last block; counters[2])
+  int *redo;                     // binary32 x2 sweep: redo[1] counts the tiles listed for
+                                 // the general split, listed from redo[redo_off] on
+  int redo_off;
+  int fold_advance;              // binary32 x2 sweep: its last block ends the step
+                                 // (k_advance's work; arrivals counted in counters[2])
 };
 
 }  // namespace fvna

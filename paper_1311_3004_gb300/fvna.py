@@ -22,7 +22,7 @@ FP64, FP32_PERT = 0, 1
 CARTESIAN, AXISYMMETRIC = 0, 1
 LIM_MC, LIM_NONE, LIM_LW = 0, 1, 2
 BC_PERIODIC, BC_EXTRAP, BC_REFLECT, BC_TAYLOR, BC_HIFU = 0, 1, 2, 3, 4
-FIELD_Q, FIELD_PRESSURE, FIELD_BUDGET, FIELD_STATS = 0, 1, 2, 3
+FIELD_Q, FIELD_PRESSURE, FIELD_BUDGET, FIELD_STATS, FIELD_CORNER = 0, 1, 2, 3, 4
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONREAL, ERR_CFL, ERR_NAN = 0, -1, -2, -3, -4, -5, -6
 ERR_SIZE = -7
@@ -96,6 +96,12 @@ def lib():
     L.fvna_step.argtypes = [vp, ctypes.c_longlong]
     L.fvna_run.restype = ctypes.c_int
     L.fvna_run.argtypes = [vp, ctypes.c_double, ctypes.c_longlong, ctypes.POINTER(Stats)]
+    L.fvna_shift.restype = ctypes.c_int
+    L.fvna_shift.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.fvna_run_moving.restype = ctypes.c_int
+    L.fvna_run_moving.argtypes = [vp, ctypes.c_double, ctypes.c_longlong, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(Stats)]
     L.fvna_sync.restype = ctypes.c_int
     L.fvna_sync.argtypes = [vp]
     L.fvna_fields.restype = ctypes.c_int
@@ -251,6 +257,23 @@ class Solver:
         d["rc"] = rc
         return d
 
+    def shift(self, domain: int, kx: int, ky: int) -> None:
+        """Move the window of one domain by (kx, ky) cells (fvna_shift)."""
+        _check(lib().fvna_shift(self._h, int(domain), int(kx), int(ky)), "fvna_shift")
+
+    def run_moving(self, t_end: float, t1: float, velocity, every: int,
+                   max_steps: int = 2 ** 62, check: bool = True) -> dict:
+        """Two-stage run: windows at rest until t1, then moving at `velocity` (fvna_run_moving)."""
+        st = Stats()
+        t_end = float(t_end) if np.isfinite(t_end) else -1e300
+        rc = lib().fvna_run_moving(self._h, t_end, int(max_steps), float(t1), float(velocity[0]),
+                                   float(velocity[1]), int(every), ctypes.byref(st))
+        if check:
+            _check(rc, "fvna_run_moving")
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
+
     def step_timed(self):
         """One step with per-kernel device times (ms): (x1 sweep, x2 sweep + source, dt update)."""
         ms = (ctypes.c_float * 3)()
@@ -285,6 +308,13 @@ class Solver:
         _check(lib().fvna_fields(self._h, domain, FIELD_BUDGET, ctypes.c_void_p(arr.ctypes.data),
                                  arr.nbytes, 0), "fvna_fields")
         return arr
+
+    def corner(self, domain: int = 0):
+        """Lower-left corner (x0, y0) of the domain's window."""
+        arr = np.zeros(2, dtype=np.float64)
+        _check(lib().fvna_fields(self._h, domain, FIELD_CORNER, ctypes.c_void_p(arr.ctypes.data),
+                                 arr.nbytes, 0), "fvna_fields")
+        return float(arr[0]), float(arr[1])
 
     def stats(self, domain: int = 0) -> dict:
         st = Stats()

@@ -122,6 +122,8 @@ def test_argument_errors_before_device_work(lib):
     assert lib.fvna_fields(None, 0, 0, None, 0, 0) == fvna.ERR_ARG
     assert lib.fvna_launch_count(None) == 0
     assert lib.fvna_step_timed(None, None) == fvna.ERR_ARG
+    assert lib.fvna_shift(None, 0, 1, 0) == fvna.ERR_ARG
+    assert lib.fvna_run_moving(None, 1.0, 1, 0.0, 1.0, 0.0, 1, None) == fvna.ERR_ARG
     lib.fvna_destroy(None)
     dp = ctypes.POINTER(ctypes.c_double)
     assert lib.fvna_riemann(5, 3.5, 1, None, None, None, None, None, None) == fvna.ERR_ARG
