@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=["gaussian", "plane", "focused", "batched", "learned",
-                                           "netfwd", "taylor"],
+                                           "netfwd", "taylor", "hifu"],
                     default="gaussian",
                     help="gaussian: the headline line; the others print their own line")
     ap.add_argument("--no-e2e", action="store_true")
@@ -504,6 +504,78 @@ def run_taylor(args):
     return 0
 
 
+def run_hifu(args):
+    """The focused packet of section 4.2 (F = 50, a = 10, 20, 30, beta = 4.8,
+    A = 4.217e-4, dt~ = 2.974e-4, nu_W = 0.9) in its two stages on a window
+    of 28 x (a + 10) wavelengths that follows the packet, binary64, eta = 20,
+    41, 82 cells per wavelength, to t = 100.  Per aperture: the on-axis
+    pressure maxima (peak value and position), their self-convergence (E_1,
+    E_inf of eta = 20 and 41 against eta = 82, evaluated as in section 4.1 on
+    the eta = 82 maxima interpolated to the coarser lab cells, x1 in [5,
+    95]), the harmonics at the focus (x1 = F, on the axis), the time to
+    solution; and the binary32 run at eta = 82 against the binary64 one."""
+    torch, fvna = _setup_cuda()
+    from paper_1311_3004_gb300 import analysis
+    t_end, etas = 100.0, [20, 41, 82]
+    amp = wl.hifu_cartesian(5.0, 10.0, window=(1.0, 1.0)).extra["amp"]
+    out, cell_updates, total_s = {}, 0.0, 0.0
+
+    def one(eta, a, prec):
+        w = wl.hifu_cartesian(eta, a)
+        e = w.extra
+        cfg = fvna.make_config(precision=prec, beta=w.beta, delta=w.delta, dx=w.dx, nu_w=w.nu_w,
+                               steps_per_graph=1)
+        dom = fvna.make_domain(w.nx, w.ny, bc=w.bc, envelope=e["envelope"], t0=e["t0"],
+                               amp=e["amp"], focal=e["focal"], aperture=e["aperture"])
+        s = fvna.Solver(cfg, [dom], [w.q0])
+        lab_cells = int((t_end - e["t1"] + w.nx * w.dx + 2) / w.dx)
+        (lab, tt, pp), sec = _timed(torch, lambda: analysis.focused_axis_run(
+            s, w.dx, e["t1"], t_end, e["focal"], lab_cells, from_bc=fvna.BC_EXTRAP))
+        steps = s.stats(0)["steps"]
+        s.close()
+        x = (np.arange(lab_cells) + 0.5) * w.dx
+        return x, lab, tt, pp, sec, steps * w.nx * w.ny
+
+    for a in (10.0, 20.0, 30.0):
+        res = {}
+        for eta in etas:
+            x, lab, tt, pp, sec, cu = one(eta, a, fvna.FP64)
+            res[eta] = (x, lab, tt, pp, sec)
+            cell_updates += cu
+            total_s += sec
+        xr, lr = res[82][0], res[82][1]
+        conv = {}
+        for eta in (20, 41):
+            x, lab = res[eta][0], res[eta][1]
+            sel = (x >= 5.0) & (x <= 95.0)
+            ref = np.interp(x[sel], xr, lr)
+            conv[str(eta)] = {"E1": float(np.sum(np.abs(lab[sel] - ref)) / np.sum(np.abs(ref))),
+                              "Einf": float(np.max(np.abs(lab[sel] - ref)) / np.max(np.abs(ref)))}
+        line = {}
+        for eta in etas:
+            x, lab, tt, pp, sec = res[eta]
+            sel = (x >= 5.0) & (x <= 95.0)
+            k = int(np.argmax(np.where(sel, lab, -np.inf)))
+            line[str(eta)] = {"peak": float(lab[k]), "peak_x1": float(x[k]),
+                              "gain": float(lab[k] / amp),
+                              "time_s": sec,
+                              "harmonics_at_focus": analysis.harmonics(tt, pp) if len(tt) > 8
+                              else None}
+        rate = {n: float(np.log(conv["20"][n] / conv["41"][n]) / np.log(41.0 / 20.0))
+                for n in ("E1", "Einf")}
+        x32, l32, _, _, sec32, _ = one(82, a, fvna.FP32_PERT)
+        sel = (x32 >= 5.0) & (x32 <= 95.0)
+        fp32 = {"time_s": sec32,
+                "axis_max_rel_err": float(np.max(np.abs(l32[sel] - lr[sel])) / np.max(lr[sel]))}
+        out[f"a={a:g}"] = {"eta": line, "self_convergence_vs_eta82": conv,
+                           "rate_20_41": rate, "fp32_eta82": fp32}
+    print(json.dumps({"metric": METRIC, "value": cell_updates / total_s, "unit": METRIC,
+                      "workload": "focused_packet_two_stage_moving_window", "dtype": "f64",
+                      "cell_updates": cell_updates, "time_s": total_s, "results": out}),
+          flush=True)
+    return 0
+
+
 def run_batched(args):
     """64 domains of uneven size in one context (one launch per sub-step over
     all of them), FP32, autotuned tiles, 1000 steps each with its own dt;
@@ -645,6 +717,8 @@ def main():
         return run_batched(args)
     if args.workload == "taylor":
         return run_taylor(args)
+    if args.workload == "hifu":
+        return run_hifu(args)
     return run_native(args)
 
 

@@ -71,8 +71,10 @@ enum fvna_field {
   FVNA_FIELD_PRESSURE = 1,  /* nx*ny binary64 p'/(rho0 c0^2) = q1 - 1 (linear EOS, section 2) */
   FVNA_FIELD_BUDGET = 2,    /* 3 binary64: sum over cells of (q1-1, q2, q3) after the last step */
   FVNA_FIELD_STATS = 3,     /* one fvna_stats */
-  FVNA_FIELD_CORNER = 4     /* 2 binary64: the window's lower-left corner (x0, y0), moved by
+  FVNA_FIELD_CORNER = 4,    /* 2 binary64: the window's lower-left corner (x0, y0), moved by
                                fvna_shift */
+  FVNA_FIELD_AXIS = 5       /* nx binary64: p'/(rho0 c0^2) = q1 - 1 along row 0 (the x1 axis
+                               of a domain whose x2-low border is a symmetry axis, section 4.2) */
 };
 
 /* ---- configuration ----------------------------------------------------- */
@@ -176,6 +178,18 @@ int fvna_fields(fvna_ctx *ctx, int domain, int what, void *dst, size_t bytes, in
  * a NULL context, a bad domain index, |kx| >= nx, |ky| >= ny, or ky != 0 in
  * the axisymmetric geometry (where x2 is the radius). */
 int fvna_shift(fvna_ctx *ctx, int domain, int kx, int ky);
+
+/* fvna_set_bc -- change the border rule of one side of one domain between
+ * steps (side 0..3: x1-low, x1-high, x2-low, x2-high).  Section 4.2's second
+ * stage turns the driven x1-low border into a zero-order extrapolation once
+ * the packet is in the domain.  The change is enqueued on the context's
+ * stream after the work already enqueued.  Returns FVNA_ERR_ARG for a bad
+ * domain, side or rule, for a periodic rule left without its partner on the
+ * opposite side (or the reverse), for a periodic or reflective rule across
+ * fewer than 3 cells, and for a driven rule (FVNA_BC_TAYLOR, FVNA_BC_HIFU)
+ * the domain was not created with on that side (its border buffers are sized
+ * at fvna_init). */
+int fvna_set_bc(fvna_ctx *ctx, int domain, int side, int bc);
 
 /* fvna_run_moving -- a two-stage run with a moving domain (section 4): the
  * window of every domain stays at rest until its time t passes t1, then

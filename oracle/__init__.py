@@ -70,6 +70,7 @@ def lib():
         L.ora_shift.restype = ctypes.c_int
         L.ora_shift.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         L.ora_corner.argtypes = [ctypes.c_void_p, dp]
+        L.ora_set_bc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         L.ora_limiter.restype = ctypes.c_double
         L.ora_limiter.argtypes = [ctypes.c_int, ctypes.c_double]
         _lib = L
@@ -134,6 +135,10 @@ class Oracle:
         """Move the window by (kx, ky) cells (moving domain, see ora_shift)."""
         if lib().ora_shift(self._h, int(kx), int(ky)) != 0:
             raise ValueError(f"shift ({kx}, {ky}) out of range")
+
+    def set_bc(self, side: int, bc: int) -> None:
+        """Border rule of one side from the next step on."""
+        lib().ora_set_bc(self._h, int(side), int(bc))
 
     def corner(self) -> tuple:
         out = np.zeros(2, dtype=np.float64)

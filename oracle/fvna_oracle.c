@@ -552,6 +552,11 @@ int ora_shift(ora_state *st, int kx, int ky) {
   return 0;
 }
 
+/* Border rule of one side (0: x1-low, 1: x1-high, 2: x2-low, 3: x2-high)
+ * from the next sub-step on: section 4.2's second stage makes the driven
+ * x1-low border a zero-order extrapolation. */
+void ora_set_bc(ora_state *st, int side, int bc) { st->p.bc[side] = bc; }
+
 /* Lower-left corner of the window: out[0] = x0, out[1] = y0. */
 void ora_corner(const ora_state *st, double *out) {
   out[0] = st->p.x0;

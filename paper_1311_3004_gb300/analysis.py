@@ -52,3 +52,56 @@ def convergence_rate(etas, errors) -> float:
     """Slope of the linear regression of log(E) on log(eta), negated (section 4.1)."""
     return float(-np.polyfit(np.log(np.asarray(etas, float)), np.log(np.asarray(errors, float)),
                              1)[0])
+
+
+def focused_axis_run(solver, dx: float, t1: float, t_end: float, probe_x1: float,
+                     lab_cells: int, extrapolate_side: int = 0, from_bc: int = 1,
+                     velocity: float = 1.0):
+    """The two stages of section 4.2 on a fvna.Solver holding one domain whose
+    x2-low border is the symmetry axis: step by step until t1 with the domain
+    at rest; then the driven x1-low border becomes a zero-order extrapolation
+    (rule `from_bc`) and the window follows the packet at `velocity` along
+    x1 in whole cells.  After every step the pressure along the axis (row 0)
+    updates the running maximum of each lab-frame cell (the on-axis pressure
+    maxima of the section) and the pressure at the lab point (probe_x1, 0) is
+    recorded.  Returns (axis maxima over lab cells 0..lab_cells-1, times,
+    probe pressures)."""
+    lab = np.full(lab_cells, -np.inf)
+    times, probe = [], []
+    switched, moved = False, 0
+    t = solver.stats(0)["t"]
+    while t < t_end:
+        st = solver.run(t_end=t_end, max_steps=1)
+        t = st["t"]
+        if not switched and t >= t1:
+            solver.set_bc(0, extrapolate_side, from_bc)
+            switched = True
+        if switched:
+            target = int(math.floor(velocity * (t - t1) / dx + 0.5))
+            if target > moved:
+                solver.shift(0, target - moved, 0)
+                moved = target
+        p = solver.axis_pressure(0)
+        k0 = moved
+        n = min(len(p), lab_cells - k0)
+        if n > 0:
+            np.maximum(lab[k0:k0 + n], p[:n], out=lab[k0:k0 + n])
+        ip = int(math.floor(probe_x1 / dx)) - k0
+        if 0 <= ip < len(p):
+            times.append(t)
+            probe.append(p[ip])
+    return lab, np.asarray(times), np.asarray(probe)
+
+
+def harmonics(times, values, n: int = 8):
+    """Amplitudes of harmonics 1..n (fundamental frequency 1) of a signal sampled
+    at uneven times: linear resampling onto a uniform grid of the mean spacing,
+    then an FFT; amplitudes at the bins nearest the integer frequencies."""
+    times = np.asarray(times, float)
+    values = np.asarray(values, float)
+    dt = float(np.mean(np.diff(times)))
+    tu = np.arange(times[0], times[-1], dt)
+    vu = np.interp(tu, times, values)
+    spec = np.abs(np.fft.rfft(vu)) * 2.0 / len(vu)
+    freq = np.fft.rfftfreq(len(vu), dt)
+    return [float(spec[int(np.argmin(np.abs(freq - k)))]) for k in range(1, n + 1)]

@@ -606,6 +606,29 @@ int fvna_shift(fvna_ctx *c, int domain, int kx, int ky) {
   return FVNA_OK;
 }
 
+int fvna_set_bc(fvna_ctx *c, int domain, int side, int bc) {
+  if (!c || domain < 0 || domain >= c->ndom || side < 0 || side > 3 || !valid_bc(bc))
+    return FVNA_ERR_ARG;
+  fvna_domain D = c->doms[domain];
+  D.bc[side] = bc;
+  const int len = side < 2 ? D.nx : D.ny;
+  if ((bc == BC_PERIODIC || bc == BC_REFLECT) && len < 3) return FVNA_ERR_ARG;
+  if ((D.bc[0] == BC_PERIODIC) != (D.bc[1] == BC_PERIODIC)) return FVNA_ERR_ARG;
+  if ((D.bc[2] == BC_PERIODIC) != (D.bc[3] == BC_PERIODIC)) return FVNA_ERR_ARG;
+  // a driven rule needs the border buffer fvna_init sized for that side
+  const DomDev &g = c->dd[domain];
+  if (bc == BC_TAYLOR && c->cfg.precision == FVNA_FP32_PERT && !g.ghost32) return FVNA_ERR_ARG;
+  if (bc == BC_HIFU && side == 0) {
+    if (c->cfg.precision == FVNA_FP64 && !g.drive) return FVNA_ERR_ARG;
+    if (c->cfg.precision == FVNA_FP32_PERT && !g.ghost32) return FVNA_ERR_ARG;
+  }
+  CK(launch_set_bc(c->d_dd, domain, side, bc, c->stream));
+  c->launches += 1;
+  c->doms[domain].bc[side] = bc;
+  c->dd[domain].bc[side] = bc;
+  return FVNA_OK;
+}
+
 int fvna_run_moving(fvna_ctx *c, double t_end, long long max_steps, double t1, double vx,
                     double vy, int every, fvna_stats *stats) {
   if (!c || max_steps < 0 || every < 1) return FVNA_ERR_ARG;
@@ -675,6 +698,25 @@ int fvna_fields(fvna_ctx *c, int domain, int what, void *dst, size_t bytes, int 
       CK(cudaMemcpyAsync(dst, c->d_stage, need, cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
     }
+    return FVNA_OK;
+  }
+  if (what == FVNA_FIELD_AXIS) {
+    const size_t need = (size_t)D.nx * sizeof(double);
+    if (bytes < need) return FVNA_ERR_ARG;
+    double *out = dst_on_device ? (double *)dst : c->d_stage;
+    if (!dst_on_device && (!c->d_stage || c->stage_bytes < need)) {
+      cudaFree(c->d_stage);
+      c->d_stage = nullptr;
+      c->stage_bytes = 0;
+      size_t mx = 0;
+      for (const auto &d : c->doms) mx = std::max(mx, (size_t)d.nx * d.ny * 3 * sizeof(double));
+      CK(cudaMalloc(&c->d_stage, mx));
+      c->stage_bytes = mx;
+      out = c->d_stage;
+    }
+    CK(launch_export(c->cfg.precision, c->dd[domain], out, 2, c->stream));
+    if (!dst_on_device) CK(cudaMemcpyAsync(dst, out, need, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return FVNA_OK;
   }
   if (what == FVNA_FIELD_CORNER) {

@@ -70,6 +70,13 @@ __global__ void k_first_dt(StepArgs A) {
   set_step_scalars(S, A);
 }
 
+// Border rule of one side of one domain (fvna_set_bc), in stream order.
+__global__ void k_set_bc(DomDev *dd, int dom, int side, int bc) { dd[dom].bc[side] = bc; }
+
+cudaError_t launch_set_bc(DomDev *dd, int dom, int side, int bc, cudaStream_t s) {
+  k_set_bc<<<1, 1, 0, s>>>(dd, dom, side, bc);
+  return cudaGetLastError();
+}
 cudaError_t launch_advance(const StepArgs &a, cudaStream_t s) {
   k_advance<<<(a.ndom + 127) / 128, 128, 0, s>>>(a);
   return cudaGetLastError();

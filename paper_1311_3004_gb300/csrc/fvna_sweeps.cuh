@@ -708,17 +708,17 @@ __global__ void k_import(DomDev D, const double *q0) {
   }
 }
 
-// what: 0 = q (3 planes, total variables), 1 = q1 - 1
+// what: 0 = q (3 planes, total variables), 1 = q1 - 1, 2 = q1 - 1 of row 0
 template <class P>
 __global__ void k_export(DomDev D, double *out, int what) {
   typedef typename P::T T;
-  const long long n = (long long)D.nx * D.ny;
+  const long long n = what == 2 ? (long long)D.nx : (long long)D.nx * D.ny;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x) {
     int j = (int)(c / D.nx), i = (int)(c - (long long)j * D.nx);
     size_t off = (size_t)j * D.pitch + i;
     double a = (double)((const T *)D.qa[0])[off];
-    if (what == 1) {
+    if (what >= 1) {
       out[c] = P::pert ? a : a - 1.0;
     } else {
       out[c] = P::pert ? 1.0 + a : a;

@@ -22,7 +22,7 @@ FP64, FP32_PERT = 0, 1
 CARTESIAN, AXISYMMETRIC = 0, 1
 LIM_MC, LIM_NONE, LIM_LW = 0, 1, 2
 BC_PERIODIC, BC_EXTRAP, BC_REFLECT, BC_TAYLOR, BC_HIFU = 0, 1, 2, 3, 4
-FIELD_Q, FIELD_PRESSURE, FIELD_BUDGET, FIELD_STATS, FIELD_CORNER = 0, 1, 2, 3, 4
+FIELD_Q, FIELD_PRESSURE, FIELD_BUDGET, FIELD_STATS, FIELD_CORNER, FIELD_AXIS = 0, 1, 2, 3, 4, 5
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONREAL, ERR_CFL, ERR_NAN = 0, -1, -2, -3, -4, -5, -6
 ERR_SIZE = -7
@@ -98,6 +98,8 @@ def lib():
     L.fvna_run.argtypes = [vp, ctypes.c_double, ctypes.c_longlong, ctypes.POINTER(Stats)]
     L.fvna_shift.restype = ctypes.c_int
     L.fvna_shift.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.fvna_set_bc.restype = ctypes.c_int
+    L.fvna_set_bc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.fvna_run_moving.restype = ctypes.c_int
     L.fvna_run_moving.argtypes = [vp, ctypes.c_double, ctypes.c_longlong, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -261,6 +263,10 @@ class Solver:
         """Move the window of one domain by (kx, ky) cells (fvna_shift)."""
         _check(lib().fvna_shift(self._h, int(domain), int(kx), int(ky)), "fvna_shift")
 
+    def set_bc(self, domain: int, side: int, bc: int) -> None:
+        """Change the border rule of one side between steps (fvna_set_bc)."""
+        _check(lib().fvna_set_bc(self._h, int(domain), int(side), int(bc)), "fvna_set_bc")
+
     def run_moving(self, t_end: float, t1: float, velocity, every: int,
                    max_steps: int = 2 ** 62, check: bool = True) -> dict:
         """Two-stage run: windows at rest until t1, then moving at `velocity` (fvna_run_moving)."""
@@ -300,6 +306,14 @@ class Solver:
         d = self.domains[domain]
         arr = np.empty((d.ny, d.nx), dtype=np.float64)
         _check(lib().fvna_fields(self._h, domain, FIELD_PRESSURE, ctypes.c_void_p(arr.ctypes.data),
+                                 arr.nbytes, 0), "fvna_fields")
+        return arr
+
+    def axis_pressure(self, domain: int = 0):
+        """p'/(rho0 c0^2) along row 0 (nx values)."""
+        d = self.domains[domain]
+        arr = np.empty(d.nx, dtype=np.float64)
+        _check(lib().fvna_fields(self._h, domain, FIELD_AXIS, ctypes.c_void_p(arr.ctypes.data),
                                  arr.nbytes, 0), "fvna_fields")
         return arr
 

@@ -213,3 +213,26 @@ def batched_64(seed: int = 4, n_domains: int = 64, n_min: int = 256, n_max: int 
         q0 = tone_burst(n, n, amplitude(p), (1.0e6 / f) / dx, ang)
         out.append((n, n, q0, {"p_pa": p, "f_hz": f, "angle": ang}))
     return out, beta_of(), delta_tilde(1.0e6), dx
+
+
+# Soft tissue, section 4.2 (after Albin et al.): delta = 6.4117e-4 m^2/s,
+# c0 = 1540 m/s, f0 = 1.1 MHz, beta = 4.8; L = one wavelength.
+def hifu_cartesian(eta: float, aperture: float, window=None, focal: float = 50.0,
+                   amp: float = 4.217e-4, delta: float = 2.974e-4, beta: float = 4.8) -> Workload:
+    """The focused packet of section 4.2 in the 2D Cartesian half plane x2 >= 0:
+    a circular-arc transducer of focal length F and half aperture a drives the
+    x1 = 0 border for 0 <= x2 <= a with the packet of eq. hifuBC (envelope
+    exp(-(tau/4)^10)), the x2 = 0 border is a symmetry (reflective) axis, the
+    other borders extrapolate.  `window` = (length along x1, height) in
+    wavelengths (default (28, a + 10)).  The run starts at t0, when the packet
+    is zero to binary64 precision at every driven point: exp(-(tau/4)^10) <
+    1e-16 for |tau| > 5.74, and tau = t + x2^2/(2F) reaches -5.74 first at
+    x2 = a.  extra["t1"] is the end of the first stage: the packet has fully
+    entered on the axis (tau > 5.74 at x1 = 0, x2 = 0)."""
+    lx, ly = window if window is not None else (28.0, aperture + 10.0)
+    nx, ny = int(round(lx * eta)), int(round(ly * eta))
+    t0 = -(5.74 + aperture * aperture / (2.0 * focal)) - 0.5
+    return Workload(f"hifu_cartesian_a{aperture:g}_eta{eta:g}", nx, ny, 0, beta, delta, 1.0 / eta,
+                    0.9, (BC_HIFU, BC_EXTRAP, BC_REFLECT, BC_EXTRAP), ambient(nx, ny),
+                    extra={"amp": amp, "focal": focal, "aperture": aperture, "envelope": 1,
+                           "t0": t0, "t1": 6.0})

@@ -123,6 +123,7 @@ def test_argument_errors_before_device_work(lib):
     assert lib.fvna_launch_count(None) == 0
     assert lib.fvna_step_timed(None, None) == fvna.ERR_ARG
     assert lib.fvna_shift(None, 0, 1, 0) == fvna.ERR_ARG
+    assert lib.fvna_set_bc(None, 0, 0, fvna.BC_EXTRAP) == fvna.ERR_ARG
     assert lib.fvna_run_moving(None, 1.0, 1, 0.0, 1.0, 0.0, 1, None) == fvna.ERR_ARG
     lib.fvna_destroy(None)
     dp = ctypes.POINTER(ctypes.c_double)

@@ -114,3 +114,25 @@ def test_moving_window_keeps_the_taylor_shock_errors(eta):
     (e1m, eim), (e1s, eis) = res
     assert abs(e1m - e1s) <= 0.02 * e1s, (e1m, e1s)
     assert abs(eim - eis) <= 0.02 * eis, (eim, eis)
+
+
+def test_set_bc_takes_effect_from_the_next_step():
+    """A border rule changed before the first step gives the run of a domain
+    created with that rule, bit for bit; changing it mid-run changes the
+    result only from then on."""
+    nx, ny = 30, 20
+    q0 = wl.random_smooth(nx, ny, 1e-3, seed=5)
+    base = dict(nx=nx, ny=ny, dx=0.1, delta=1e-3)
+    o1 = oracle.Oracle(Params(bc=(BC_EXTRAP,) * 4, **base), q0)
+    o2 = oracle.Oracle(Params(bc=(oracle.BC_REFLECT, BC_EXTRAP, BC_EXTRAP, BC_EXTRAP), **base), q0)
+    o2.set_bc(0, BC_EXTRAP)
+    o1.run(15)
+    o2.run(15)
+    assert np.array_equal(o1.q(), o2.q())
+    o3 = oracle.Oracle(Params(bc=(BC_EXTRAP,) * 4, **base), q0)
+    o3.run(5)
+    o3.set_bc(1, oracle.BC_REFLECT)
+    o3.run(10)
+    assert not np.array_equal(o3.q(), o1.q())
+    for o in (o1, o2, o3):
+        o.close()
