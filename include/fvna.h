@@ -199,8 +199,10 @@ int fvna_set_bc(fvna_ctx *ctx, int domain, int side, int bc);
  * after each chunk a domain whose window lags the target displacement
  * (round(vx (t - t1) / dx), round(vy (t - t1) / dx)) cells, counted from
  * where the window was when the context was created, is moved by the
- * difference with fvna_shift.  Stops at t_end, after max_steps steps, or at
- * the first device error, like fvna_run (same return codes; stats as there).
+ * difference with fvna_shift (the count includes the caller's own
+ * fvna_shift calls).  Stops at t_end (with several domains, once the first of
+ * them reaches it), after max_steps steps, or at the first device error, like
+ * fvna_run (same return codes; stats as there).
  * FVNA_ERR_ARG if every < 1, or for a shift fvna_shift would refuse. */
 int fvna_run_moving(fvna_ctx *ctx, double t_end, long long max_steps, double t1, double vx,
                     double vy, int every, fvna_stats *stats);
