@@ -782,8 +782,13 @@ __global__ void __launch_bounds__(32, Y32_MINBLOCKS) k_sweep_y32(StepArgs A) {
   const Maps *maps = (const Maps *)A.tmaps;
   const int nredo = REDO ? A.redo[1] : 0;
   if (REDO && nredo == 0) {
-    if (blockIdx.x == 0 && lane == 0) A.redo[0] = 0;
-    y32_finish_step(A, lane, false);
+    // nothing to redo: every statistic of the step is in (the first kernel
+    // has completed), so block 0 alone ends the step, without arrivals
+    if (blockIdx.x == 0) {
+      if (lane == 0) A.redo[0] = 0;
+      if (A.fold_advance)
+        for (int d = lane; d < A.ndom; d += 32) advance_domain(A, d);
+    }
     return;
   }
   if (lane == 0)
