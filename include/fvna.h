@@ -66,6 +66,11 @@ enum fvna_bc {
   FVNA_BC_TAYLOR = 3,    /* Taylor-shock values of eq. OurTaylorS (section 4.1) */
   FVNA_BC_HIFU = 4       /* focused drive of eq. hifuBC on the x1-low border */
 };
+enum fvna_splitting {
+  FVNA_SPLIT_GODUNOV = 0,  /* x1 sweep, x2 sweep, source, each over dt (section 3, eqs. fs:*) */
+  FVNA_SPLIT_STRANG = 1    /* x1 sweep over dt/2, x2 sweep, source, x1 sweep over dt/2: the
+                              symmetric (second-order) order of the same fractional steps */
+};
 enum fvna_field {
   FVNA_FIELD_Q = 0,         /* 3*nx*ny binary64 total variables */
   FVNA_FIELD_PRESSURE = 1,  /* nx*ny binary64 p'/(rho0 c0^2) = q1 - 1 (linear EOS, section 2) */
@@ -94,6 +99,8 @@ typedef struct fvna_config {
   int tile_y;           /* x2-sweep tile height (rows per warp); 0 = default */
   int compensated;      /* FVNA_FP32_PERT: 1 = sum each cell update with error-free
                            two-sums (one final rounding), 0 = as written */
+  int splitting;        /* enum fvna_splitting */
+  int reserved;         /* 0 */
 } fvna_config;
 
 /* One domain.  Coordinates are those of the lower-left corner of cell (0,0);
@@ -211,7 +218,8 @@ int fvna_run_moving(fvna_ctx *ctx, double t_end, long long max_steps, double t1,
  * from the step graph), CUDA events recorded between them on the context's
  * stream, and block until it is done.  ms receives the device time of each
  * launch in milliseconds: ms[0] x1 sweep (a plain copy if that sweep is off), ms[1] x2
- * sweep + source, ms[2] dt update.  The step is identical to one of
+ * sweep + source, ms[2] dt update (with FVNA_SPLIT_STRANG: also the second
+ * x1 sweep and the copy that ends the step).  The step is identical to one of
  * fvna_step.  Returns FVNA_OK or the device status after the step. */
 int fvna_step_timed(fvna_ctx *ctx, float ms[3]);
 
@@ -277,8 +285,8 @@ int fvna_riemann(int precision, double beta, int n, const double *qL, const doub
  * blocks until its step is done.  All calls share the array and each call
  * clears what must start at zero, but calls that overlap on the GPU (two host
  * threads, or several streams) race on it.  Results equal those of
- * fvna_step with cfg->dt_fixed = dt.  Returns FVNA_OK, FVNA_ERR_ARG,
- * FVNA_ERR_SIZE for a larger domain, FVNA_ERR_NONREAL / FVNA_ERR_NAN from the
+ * fvna_step with cfg->dt_fixed = dt.  Returns FVNA_OK, FVNA_ERR_ARG (also for
+ * cfg->splitting other than FVNA_SPLIT_GODUNOV), FVNA_ERR_SIZE for a larger domain, FVNA_ERR_NONREAL / FVNA_ERR_NAN from the
  * step, or FVNA_ERR_CUDA. */
 #define FVNA_NOALLOC_MAX_CELLS 524288
 int fvna_step_noalloc(const fvna_config *cfg, const fvna_domain *dom, const double *q_in,
@@ -330,7 +338,8 @@ void fvna_net_destroy(fvna_net *net);
  * (q1-1, q2, q3)) to the state, except on the cells within edge_band cells of
  * a domain edge (a network trained on crops with a loss margin has not learnt
  * them); net = NULL detaches.  The network is borrowed and must outlive its
- * use. */
+ * use.  FVNA_ERR_ARG with FVNA_SPLIT_STRANG (the correction follows the
+ * Godunov step it was trained on). */
 int fvna_set_correction(fvna_ctx *ctx, fvna_net *net, float in_scale, float out_scale,
                         int every, int edge_band);
 

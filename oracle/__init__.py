@@ -47,7 +47,8 @@ class _Params(ctypes.Structure):
                 ("dt_fixed", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
                 ("t0", ctypes.c_double), ("taylor_ratio", ctypes.c_double),
                 ("taylor_angle", ctypes.c_double), ("amp", ctypes.c_double),
-                ("focal", ctypes.c_double), ("aperture", ctypes.c_double)]
+                ("focal", ctypes.c_double), ("aperture", ctypes.c_double),
+                ("splitting", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 _lib = None
@@ -105,6 +106,8 @@ class Params:
     amp: float = 0.0
     focal: float = 1.0
     aperture: float = 0.0
+    splitting: int = 0          # 0 Godunov, 1 Strang
+    reserved: int = 0
 
     def to_c(self) -> _Params:
         p = _Params()

@@ -28,7 +28,10 @@
  *   - the CFL maximum is over |s|, over the faces of the domain cells only;
  *   - two ghost layers, refilled from the current state before every
  *     sub-step; driven borders are evaluated at t_n for all three sub-steps;
- *   - Godunov splitting x1 -> x2 -> source in every step, one dt;
+ *   - Godunov splitting x1 -> x2 -> source in every step, one dt (or, on
+ *     request, Strang's symmetric form x1(dt/2) -> x2 -> source -> x1(dt/2),
+ *     a second-order variant of the consecutive application that section 3
+ *     describes; the paper does not say which order it uses);
  *   - if W.W == 0 the limited wave is zero; at s == 0 the upwind side is i+1;
  *   - dt_0 comes from a speed-only pass over Q^0; a step that would pass
  *     t_end is shortened to end on it; nu_n > nu_max is an error, not a retry.
@@ -85,6 +88,8 @@ typedef struct {
   double amp;         /* HIFU drive amplitude A (eq. hifuBC) */
   double focal;       /* focal length F */
   double aperture;    /* half aperture a */
+  int splitting;      /* 0: Godunov x1, x2, source; 1: Strang x1(dt/2), x2, source, x1(dt/2) */
+  int reserved;
 } ora_params;
 
 typedef struct {
@@ -468,9 +473,10 @@ long ora_run(ora_state *st, double t_end, long max_steps) {
     if (timed && st->t + dt >= t_end) { dt = t_end - st->t; last = 1; }
     double lam = dt / p->dx;
     double smax = 0.0;
+    const int strang = p->splitting == 1;
     if (p->sweeps & 1) {
       fill_ghosts(st, st->t);
-      smax = max_nan(smax, sweep(st, 0, lam));
+      smax = max_nan(smax, sweep(st, 0, strang ? lam * 0.5 : lam));
     }
     if (p->sweeps & 2) {
       fill_ghosts(st, st->t);
@@ -479,6 +485,10 @@ long ora_run(ora_state *st, double t_end, long max_steps) {
     if (p->sweeps & 4) {
       fill_ghosts(st, st->t);
       source(st, dt);
+    }
+    if (strang && (p->sweeps & 1)) {
+      fill_ghosts(st, st->t);
+      smax = max_nan(smax, sweep(st, 0, lam * 0.5));
     }
     if (smax != smax) st->status |= ST_NAN;
     st->smax = smax;

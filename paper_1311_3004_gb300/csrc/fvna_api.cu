@@ -103,6 +103,7 @@ int validate(const fvna_config *c, int n, const fvna_domain *d, const double *co
   if (c->tile_x != 0 && c->tile_x != 16 && c->tile_x != 32 && c->tile_x != 64) return FVNA_ERR_ARG;
   if (c->tile_y != 0 && (c->tile_y < 8 || c->tile_y > 4096)) return FVNA_ERR_ARG;
   if (c->compensated != 0 && c->compensated != 1) return FVNA_ERR_ARG;
+  if (c->splitting != FVNA_SPLIT_GODUNOV && c->splitting != FVNA_SPLIT_STRANG) return FVNA_ERR_ARG;
   for (int k = 0; k < n; k++) {
     const fvna_domain &D = d[k];
     if (D.nx < 1 || D.ny < 1 || D.nx > (1 << 20) || D.ny > (1 << 20)) return FVNA_ERR_ARG;
@@ -172,6 +173,11 @@ int enqueue_steps_raw(fvna_ctx *c, cudaStream_t s, int nsteps) {
     if (rc != FVNA_OK) return rc;
     CK(sweep_x(c, s));
     CK(sweep_y(c, s));
+    if (c->cfg.splitting == FVNA_SPLIT_STRANG) {
+      // the second half x1 sweep, then its result back into the state planes
+      CK(sweep_x(c, s));
+      CK(launch_copy_back(c->args, c->cfg.precision == FVNA_FP64 ? 8 : 4, s));
+    }
     if (c->net) {
       const DomDev &d = c->dd[0];
       size_t pix = (size_t)d.nx * d.ny;
@@ -508,7 +514,11 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   c->args_y.ntiles = c->nty;
   c->args_y.redo_off = 2;
   c->args_y.sweep = 1;
-  c->args_y.fold_advance = prec == FVNA_FP32_PERT ? 1 : 0;
+  // Strang: the step ends after the second x1 sweep, so never in the x2 sweep
+  const bool strang = cfg->splitting == FVNA_SPLIT_STRANG;
+  c->args_x.x_half = strang ? 1 : 0;
+  c->args_y.fold_advance = prec == FVNA_FP32_PERT && !strang ? 1 : 0;
+  if (strang) c->kernels_per_step += prec == FVNA_FP32_PERT ? 3 : 2;
 
 
   // initial state
@@ -778,6 +788,11 @@ int fvna_step_timed(fvna_ctx *c, float ms[3]) {
   if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
   if (e == cudaSuccess) e = sweep_y(c, c->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->stream);
+  if (e == cudaSuccess && c->cfg.splitting == FVNA_SPLIT_STRANG) {
+    e = sweep_x(c, c->stream);
+    if (e == cudaSuccess)
+      e = launch_copy_back(c->args, c->cfg.precision == FVNA_FP64 ? 8 : 4, c->stream);
+  }
   if (e == cudaSuccess && !c->args_y.fold_advance) e = launch_advance(c->args, c->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[3], c->stream);
   if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
@@ -850,6 +865,7 @@ int fvna_set_correction(fvna_ctx *c, fvna_net *net, float in_scale, float out_sc
                         int edge_band) {
   if (!c || every < 1 || edge_band < 0) return FVNA_ERR_ARG;
   if (net && (c->ndom != 1 || c->cfg.precision != FVNA_FP32_PERT)) return FVNA_ERR_ARG;
+  if (net && c->cfg.splitting != FVNA_SPLIT_GODUNOV) return FVNA_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));
   if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
   if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }

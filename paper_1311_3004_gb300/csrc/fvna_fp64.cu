@@ -70,6 +70,31 @@ __global__ void k_first_dt(StepArgs A) {
   set_step_scalars(S, A);
 }
 
+// End of a Strang step: the second x1 sweep left the state in the swept
+// planes; copy them back (word by word, whatever the precision) for every
+// domain still running, and reset the x1 sweep's tile counter (binary32),
+// which no x2 sweep resets before the next step.
+__global__ void k_copy_back(StepArgs A, int esz) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && A.counters) A.counters[0] = 0u;
+  for (int d = 0; d < A.ndom; d++) {
+    if (A.scal[d].done) continue;
+    const DomDev &D = A.doms[d];
+    const size_t words = (size_t)D.ny * D.pitch * esz / 4;
+    for (int k = 0; k < 3; k++) {
+      const unsigned *src = (const unsigned *)D.qb[k];
+      unsigned *dst = (unsigned *)D.qa[k];
+      for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < words;
+           i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+    }
+  }
+}
+
+cudaError_t launch_copy_back(const StepArgs &a, int esz, cudaStream_t s) {
+  k_copy_back<<<1024, 256, 0, s>>>(a, esz);
+  return cudaGetLastError();
+}
+
 // Border rule of one side of one domain (fvna_set_bc), in stream order.
 __global__ void k_set_bc(DomDev *dd, int dom, int side, int bc) { dd[dom].bc[side] = bc; }
 

@@ -31,6 +31,9 @@ cudaError_t launch_drive_fp32(const StepArgs &a, int dom, int ny, int always, cu
 cudaError_t launch_first_dt(const StepArgs &a, cudaStream_t s);
 cudaError_t launch_import(int precision, const DomDev &d, const double *q0, cudaStream_t s);
 cudaError_t launch_export(int precision, const DomDev &d, double *out, int what, cudaStream_t s);
+// end of a Strang step: swept planes back into the state planes (esz: bytes
+// per value), the x1 sweep's tile counter reset
+cudaError_t launch_copy_back(const StepArgs &a, int esz, cudaStream_t s);
 // border rule of one side of one domain in the device descriptors
 cudaError_t launch_set_bc(DomDev *dd, int dom, int side, int bc, cudaStream_t s);
 // moving domain: shift the window of domain dom by (kx, ky) cells (two

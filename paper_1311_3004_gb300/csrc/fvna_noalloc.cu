@@ -100,6 +100,7 @@ extern "C" int fvna_step_noalloc(const fvna_config *cfg, const fvna_domain *dom,
   if (cfg->geometry != FVNA_CARTESIAN && cfg->geometry != FVNA_AXISYMMETRIC) return FVNA_ERR_ARG;
   if (cfg->limiter < FVNA_LIM_MC || cfg->limiter > FVNA_LIM_LW) return FVNA_ERR_ARG;
   if (cfg->sweeps < 0 || cfg->sweeps > 7 || !(cfg->dx > 0.0) || !(dt > 0.0)) return FVNA_ERR_ARG;
+  if (cfg->splitting != FVNA_SPLIT_GODUNOV) return FVNA_ERR_ARG;   // takes the Godunov step
   const int nx = dom->nx, ny = dom->ny;
   if (nx < 1 || ny < 1) return FVNA_ERR_ARG;
   for (int s = 0; s < 4; s++) {

@@ -286,7 +286,8 @@ __global__ void __launch_bounds__(128, FVNA_X_MINBLOCKS) k_sweep_x(StepArgs A) {
     DomScal *S = A.scal + tl.dom;
     if (S->done) continue;
     const double t = S->t;
-    const T lam = P::pert ? (T)S->lam32 : (T)S->lam;
+    // dt/dx, halved (exactly) for the two x1 sweeps of a Strang step
+    const T lam = (P::pert ? (T)S->lam32 : (T)S->lam) * (A.x_half ? (T)0.5 : (T)1);
     const int nx = D.nx, ny = D.ny;
     const T *qi[3] = {(const T *)D.qa[0], (const T *)D.qa[1], (const T *)D.qa[2]};
     T *qo[3] = {(T *)D.qb[0], (T *)D.qb[1], (T *)D.qb[2]};

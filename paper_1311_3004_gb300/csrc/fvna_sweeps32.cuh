@@ -250,7 +250,8 @@ __device__ __forceinline__ bool x32_tile(const StepArgs &A, const DomDev &D, Dom
     }
   }
   March<LIM, COMP, SPEC> m;
-  m.init((float)A.beta, S->lam32);
+  // dt/dx, halved (exactly) for the two x1 sweeps of a Strang step
+  m.init((float)A.beta, A.x_half ? 0.5f * S->lam32 : S->lam32);
   // cells x0+SW, x0+SW+1 (right neighbours of the first half) before the
   // second half overwrites them
   float2 rA[3];

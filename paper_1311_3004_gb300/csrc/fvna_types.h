@@ -72,7 +72,7 @@ struct StepArgs {
   double beta, delta, dx, nu_w, nu_max, dt_fixed;
   int limiter, geometry, sweeps, tile_y;
   int compensated;               // binary32 update with error-free two-sums
-  int pad_;
+  int x_half;                    // 1: the x1 sweep advances dt/2 (Strang splitting)
   const void *tmaps;             // binary32 sweeps: TMA tensor maps, one set per domain
   unsigned *counters;            // binary32 sweeps: next-tile counters of the x1 and x2 sweeps
   int sweep;                     // 0: x1 sweep, 1: x2 sweep

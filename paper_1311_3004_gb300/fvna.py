@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfvna.so")
 FP64, FP32_PERT = 0, 1
 CARTESIAN, AXISYMMETRIC = 0, 1
 LIM_MC, LIM_NONE, LIM_LW = 0, 1, 2
+SPLIT_GODUNOV, SPLIT_STRANG = 0, 1
 BC_PERIODIC, BC_EXTRAP, BC_REFLECT, BC_TAYLOR, BC_HIFU = 0, 1, 2, 3, 4
 FIELD_Q, FIELD_PRESSURE, FIELD_BUDGET, FIELD_STATS, FIELD_CORNER, FIELD_AXIS = 0, 1, 2, 3, 4, 5
 
@@ -45,7 +46,8 @@ class Config(ctypes.Structure):
                 ("beta", ctypes.c_double), ("delta", ctypes.c_double), ("dx", ctypes.c_double),
                 ("nu_w", ctypes.c_double), ("nu_max", ctypes.c_double),
                 ("dt_fixed", ctypes.c_double), ("steps_per_graph", ctypes.c_int),
-                ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("compensated", ctypes.c_int)]
+                ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("compensated", ctypes.c_int),
+                ("splitting", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class Domain(ctypes.Structure):
@@ -165,9 +167,9 @@ def _check(rc: int, where: str) -> int:
 
 def make_config(precision=FP64, geometry=CARTESIAN, limiter=LIM_MC, sweeps=7, beta=3.5,
                 delta=0.0, dx=1.0, nu_w=0.9, nu_max=1.0, dt_fixed=0.0, steps_per_graph=0,
-                tile_x=0, tile_y=0, compensated=1) -> Config:
+                tile_x=0, tile_y=0, compensated=1, splitting=0) -> Config:
     return Config(precision, geometry, limiter, sweeps, beta, delta, dx, nu_w, nu_max, dt_fixed,
-                  steps_per_graph, tile_x, tile_y, compensated)
+                  steps_per_graph, tile_x, tile_y, compensated, splitting, 0)
 
 
 def make_domain(nx, ny, bc=(BC_EXTRAP,) * 4, envelope=0, x0=0.0, y0=0.0, t0=0.0, dt0=0.0,
