@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -665,6 +666,10 @@ int fvna_run_moving(fvna_ctx *c, double t_end, long long max_steps, double t1, d
       const long long ty = (long long)std::floor(vy * e / c->cfg.dx + 0.5);
       const long long kx = tx - c->moved_x[d], ky = ty - c->moved_y[d];
       if (kx == 0 && ky == 0) continue;
+      if (std::llabs(kx) >= c->doms[d].nx || std::llabs(ky) >= c->doms[d].ny) {
+        rc = FVNA_ERR_ARG;   // the window would leave its whole width behind
+        break;
+      }
       rc = fvna_shift(c, d, (int)kx, (int)ky);
       if (rc != FVNA_OK) break;
     }
