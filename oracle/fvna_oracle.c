@@ -23,7 +23,7 @@
  *                  - dt/dx (F~_{i+1/2} - F~_{i-1/2})               eq. fv-hr
  *   dt        dt_{n+1} = nu_W dx / max|s| of step n                 section 4
  *
- * Readings where the paper is silent (each also listed in the design notes):
+ * Readings where the paper is silent:
  *   - the source uses lap(q2/q1), the Laplacian of the velocity z2;
  *   - the CFL maximum is over |s|, over the faces of the domain cells only;
  *   - two ghost layers, refilled from the current state before every

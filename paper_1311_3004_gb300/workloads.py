@@ -185,7 +185,8 @@ def focused_axisym(nz: int = 4096, nr: int = 1024, cells_per_wavelength: float =
     L = one wavelength, so the aperture is 20 and the focal length 40."""
     lam = C0 / freq
     q0 = ambient(nz, nr)
-    # CFL 0.4: the axisymmetric step is stable up to about 0.5 (see the design notes)
+    # CFL 0.4: with the first-order flux on the two radial faces next to the
+    # axis, the linearised axisymmetric step is stable up to CFL 0.5
     w = Workload(f"focused_axisym_{nz}x{nr}", nz, nr, 0, beta_of(), delta_tilde(freq),
                  1.0 / cells_per_wavelength, 0.4, (BC_HIFU, BC_EXTRAP, BC_REFLECT, BC_EXTRAP), q0,
                  geometry=1,
