@@ -49,7 +49,7 @@ int main(void) {
   printf("fvna_config %zu\nfvna_domain %zu\nfvna_stats %zu\n", sizeof(fvna_config),
          sizeof(fvna_domain), sizeof(fvna_stats));
   P(fvna_config, beta); P(fvna_config, dt_fixed); P(fvna_config, tile_y);
-  P(fvna_config, compensated);
+  P(fvna_config, compensated); P(fvna_config, splitting);
   P(fvna_domain, x0); P(fvna_domain, dt0); P(fvna_domain, aperture);
   P(fvna_stats, nu_std); P(fvna_stats, status);
   return 0;
