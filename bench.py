@@ -67,6 +67,8 @@ def parse():
                     help="x2-sweep tile height (0: the library's choice)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--splitting", choices=["godunov", "strang"], default="godunov",
+                    help="order of the fractional steps (the paper's: godunov)")
     ap.add_argument("--plain-update", action="store_true",
                     help="FP32 cell update as written instead of the compensated sum")
     ap.add_argument("--flush-mb", type=int, default=512,
@@ -230,11 +232,11 @@ def peaks():
 
 
 def measure_precision(torch, fvna, w, precision, steps, warmup, flush, do_flush=True,
-                      compensated=1, tiles=(0, 0)):
+                      compensated=1, tiles=(0, 0), splitting=0):
     stream = torch.cuda.current_stream()
     cfg = fvna.make_config(precision=precision, beta=w.beta, delta=w.delta, dx=w.dx,
                            nu_w=w.nu_w, steps_per_graph=1, compensated=compensated,
-                           tile_x=tiles[0], tile_y=tiles[1])
+                           tile_x=tiles[0], tile_y=tiles[1], splitting=splitting)
     s = fvna.Solver(cfg, [fvna.make_domain(w.nx, w.ny, bc=w.bc)], [w.q0],
                     stream=stream.cuda_stream)
     for _ in range(warmup):
@@ -280,7 +282,8 @@ def run_native(args):
         per, launches, st = measure_precision(torch, fvna, w, prec, args.steps, args.warmup,
                                               flush, args.flush_mb > 0,
                                               0 if args.plain_update else 1,
-                                              (args.tile_x, args.tile_y))
+                                              (args.tile_x, args.tile_y),
+                                              1 if args.splitting == "strang" else 0)
     torch.cuda.synchronize()
     step_ms = per.sum(axis=1)
     from paper_1311_3004_gb300.replicas import job_throughput
@@ -314,6 +317,7 @@ def run_native(args):
         "config": {"workload": f"gaussian_pulse_{w.nx}x{w.ny}", "cells_per_gpu": cells,
                    "precision": args.precision, "time_steps_per_bench_step": 1,
                    "compensated_update": (not args.plain_update) and args.precision == "fp32",
+                   "splitting": args.splitting,
                    "l2": (f"flushed before every timed step ({args.flush_mb} MB write)"
                           if args.flush_mb > 0 else "not flushed"),
                    "parallelism": f"replicas x{world}"},
@@ -324,10 +328,12 @@ def run_native(args):
     }
 
     if not args.no_e2e:
-        line["e2e"] = e2e(torch, fvna, w, prec, 0 if args.plain_update else 1)
+        line["e2e"] = e2e(torch, fvna, w, prec, 0 if args.plain_update else 1,
+                          splitting=1 if args.splitting == "strang" else 0)
     if prec == fvna.FP32_PERT and not args.no_fp64:
         per64, _, _ = measure_precision(torch, fvna, w, fvna.FP64, max(3, args.steps // 10), 2,
-                                        flush, args.flush_mb > 0)
+                                        flush, args.flush_mb > 0,
+                                        splitting=1 if args.splitting == "strang" else 0)
         line["fp64"] = {"value": cells * len(per64) / (per64.sum() / 1e3),
                         "ms_per_step": float(per64.sum(axis=1).mean()),
                         "kernel_ms": [float(x) for x in per64.mean(axis=0)]}
@@ -340,13 +346,13 @@ def run_native(args):
     return 0
 
 
-def e2e(torch, fvna, w, prec, compensated=1, reps=2):
+def e2e(torch, fvna, w, prec, compensated=1, reps=2, splitting=0):
     """Whole-run call sequence from pinned host memory, host wall clock."""
     cells = w.nx * w.ny
     q_host = torch.from_numpy(w.q0).pin_memory()
     out = torch.empty((3, w.ny, w.nx), dtype=torch.float64).pin_memory()
     cfg = fvna.make_config(precision=prec, beta=w.beta, delta=w.delta, dx=w.dx, nu_w=w.nu_w,
-                           steps_per_graph=64, compensated=compensated)
+                           steps_per_graph=64, compensated=compensated, splitting=splitting)
     times = []
     for _ in range(reps):
         torch.cuda.synchronize()
