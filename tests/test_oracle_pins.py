@@ -417,6 +417,40 @@ def test_plane_wave_steepens_as_poisson_solution():
     assert errs[0] > errs[1] > errs[2], errs
 
 
+# ---------------------------------------------------------------- focused drive (section 4.2)
+
+def _axis_maxima(eta, t_end, focal=20.0, aperture=8.0):
+    w = wl.hifu_cartesian(eta, aperture, window=(30.0, 15.0), focal=focal)
+    e = w.extra
+    p = Params(nx=w.nx, ny=w.ny, bc=w.bc, beta=w.beta, delta=w.delta, dx=w.dx, nu_w=0.9,
+               t0=e["t0"], amp=e["amp"], focal=focal, aperture=aperture, envelope=1)
+    o = oracle.Oracle(p, w.q0)
+    top = np.full(w.nx, -np.inf)
+    while o.scalars()["t"] < t_end:
+        o.run(1, t_end)
+        np.maximum(top, o.q()[0, 0] - 1.0, out=top)
+    o.close()
+    return (np.arange(w.nx) + 0.5) * w.dx, top / e["amp"]
+
+
+def test_focused_drive_converges_on_the_axis():
+    """The drive of eq. hifuBC delays the outer part of the aperture by
+    x2^2 / (2F), a cylindrical wave converging on (F, 0); with the x2 = 0
+    border as symmetry axis, the on-axis peak pressure near the border grows
+    as sqrt(F / (F - d)) (energy of a converging cylindrical wave), and the
+    on-axis maxima peak just short of the focus with a gain above 1.5 (F = 20,
+    a = 8 wavelengths; a drive delayed the wrong way would diverge)."""
+    x, top = _axis_maxima(20.0, 7.0)
+    i = int(round(1.0 / 0.05))          # cell centred at x1 = 1.025
+    expect = np.sqrt(20.0 / (20.0 - x[i]))
+    assert abs(top[i] / expect - 1.0) < 0.02, (top[i], expect)
+    x, top = _axis_maxima(10.0, 32.0)
+    k = int(np.argmax(top))
+    assert 0.8 * 20.0 < x[k] < 20.0, x[k]
+    assert top[k] > 1.5, top[k]
+    assert np.all(top[: int(round(5.0 / 0.1))] < 1.3)
+
+
 # ---------------------------------------------------------------- axisymmetric
 
 def test_axisymmetric_source_terms_exact():
