@@ -72,6 +72,8 @@ def lib():
         L.ora_shift.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         L.ora_corner.argtypes = [ctypes.c_void_p, dp]
         L.ora_set_bc.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+        L.ora_drive.argtypes = [ctypes.POINTER(_Params), ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, dp]
         L.ora_limiter.restype = ctypes.c_double
         L.ora_limiter.argtypes = [ctypes.c_int, ctypes.c_double]
         _lib = L
@@ -181,6 +183,15 @@ def interface(beta: float, qL, qR):
     ap = np.zeros(3)
     nr = lib().ora_interface(beta, _dptr(qL), _dptr(qR), _dptr(s), _dptr(W), _dptr(am), _dptr(ap))
     return s, W.reshape(3, 3), am, ap, bool(nr)
+
+
+def drive(params: Params, x1: float, x2: float, t: float) -> np.ndarray:
+    """Border values (q1, q2, q3) of the focused drive of eq. hifuBC at (x1, x2)
+    and time t, with the amplitude, focal length and envelope of `params`."""
+    p = params.to_c()
+    out = np.zeros(3)
+    lib().ora_drive(ctypes.byref(p), float(x1), float(x2), float(t), _dptr(out))
+    return out
 
 
 def limiter(kind: int, theta: float) -> float:

@@ -620,5 +620,12 @@ int ora_interface(double beta, const double *qL, const double *qR, double *s, do
   return nr;
 }
 
+/* The driven border values of eq. hifuBC at (x1, x2, t) with the parameters
+ * amplitude, focal length and envelope kind, whether or not (x1, x2) lies in
+ * the aperture (for the pins): out = (q1, q2, q3). */
+void ora_drive(const ora_params *p, double x1, double x2, double t, double *out) {
+  hifu_value(p, x1, x2, t, out);
+}
+
 /* Evaluate the limiter function (for the pins). */
 double ora_limiter(int kind, double theta) { return limiter_phi(kind, theta); }

@@ -451,6 +451,126 @@ def test_focused_drive_converges_on_the_axis():
     assert np.all(top[: int(round(5.0 / 0.1))] < 1.3)
 
 
+def _g(kind, tau, amp=1.0, focal=50.0):
+    """g of eq. hifuBC on the axis at the border (x1 = x2 = 0), where tau = t."""
+    return oracle.drive(Params(nx=1, ny=1, amp=amp, focal=focal, envelope=kind), 0.0, 0.0, tau)[0] - 1.0
+
+
+def _envelope(kind, tau):
+    """The envelope alone: g / (A sin(2 pi tau)), at tau away from the zeros of the sine."""
+    return _g(kind, tau) / np.sin(2.0 * np.pi * tau)
+
+
+def test_one_sided_drive_envelope():
+    """The one-sided turn-on read from eq. hifuBC, E(tau) = exp(-(tau/4)^-10)
+    for tau > 0: nothing before the drive starts (tau <= 0, and numerically
+    nothing for the first periods: the turn-on is flat to all orders), a
+    full-amplitude sine long after it (a flipped exponent would grow past 1,
+    the packet form would die out), the 1/e point at four periods (the 1/4
+    scale), and the power law -ln E = (tau/4)^-10 (log-log slope -10)."""
+    for tau in (-5.25, -3.25, -1.75, -0.25, -1e-9, 0.0):
+        assert _g(0, tau) == 0.0
+    assert _g(0, 0.25) == 0.0 and abs(_g(0, 1.25)) < 1e-250
+    long = [_g(0, k + 0.25) for k in (40, 60, 80)]
+    assert all(abs(v - 1.0) < 1e-9 for v in long), long
+    assert all(v <= 1.0 for v in long)
+    assert abs(_g(0, 40.75) + 1.0) < 1e-9
+    # the 1/e crossing of E, by bisection on E(tau) - 1/e over tau in [3.2, 4.8]
+    lo, hi = 3.2, 4.8
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if _envelope(0, mid) < np.exp(-1.0):
+            lo = mid
+        else:
+            hi = mid
+    assert abs(lo - 4.0) < 1e-7, lo   # E = g / sin loses digits next to the zero of sin(8 pi)
+    # log-log slope of -ln E against tau
+    t1, t2 = 3.1, 6.3
+    slope = (np.log(-np.log(_envelope(0, t2))) - np.log(-np.log(_envelope(0, t1)))) / \
+        (np.log(t2) - np.log(t1))
+    assert abs(slope + 10.0) < 1e-6, slope
+    # the packet form is the mirror image in log tau: E_packet(4 s) = E_turn-on(4 / s)
+    for s_ in (0.77, 1.3):
+        assert abs(_envelope(1, 4.0 * s_) - _envelope(0, 4.0 / s_)) < 1e-12
+
+
+def test_drive_momentum_points_at_the_focus():
+    """Eq. hifuBC puts the momentum of the border value along the line from the
+    border point (0, x2) to the focus (F, 0), with magnitude |g|: the linear
+    relation q_n = q1 - 1 of a wave travelling that way.  The delay x2^2/(2F)
+    is the paraxial form of the path difference sqrt(F^2 + x2^2) - F, and a
+    ghost centre a distance d behind the border sees the border's drive d
+    later (propagation at unit speed in +x1)."""
+    F, A = 40.0, 3e-4
+    P = Params(nx=1, ny=1, amp=A, focal=F, envelope=0)
+    for x2 in (0.5, 3.0, 11.0):
+        q = oracle.drive(P, 0.0, x2, 9.13)
+        g = q[0] - 1.0
+        assert abs(g) > 1e-5
+        d = np.array([F, -x2]) / np.hypot(F, x2)
+        assert np.allclose(q[1:], g * d, rtol=1e-10, atol=0.0)   # g = q1 - 1 keeps ~12 digits
+        # paraxial delay: the drive equals the on-axis one at the geometric
+        # delay, to the order x2^4 / (8 F^3) of the paraxial expansion
+        geo = np.hypot(F, x2) - F
+        g_axis = oracle.drive(P, 0.0, 0.0, 9.13 + geo)[0] - 1.0
+        bound = A * 2.0 * np.pi * (x2 ** 4 / (8.0 * F ** 3)) * 1.01 + 1e-18
+        assert abs(g - g_axis) <= bound, (x2, g, g_axis, bound)
+        # the sign of the delay: the outer aperture fires first (checked where
+        # twice the delay is well short of a period)
+        if x2 <= 3.0:
+            assert abs(oracle.drive(P, 0.0, 0.0, 9.13 - geo)[0] - 1.0 - g) > 10 * bound
+    for d_ in (0.5 / 20, 2.5 / 20):
+        a = oracle.drive(P, -d_, 2.0, 9.13)
+        b = oracle.drive(P, 0.0, 2.0, 9.13 + d_)
+        assert np.array_equal(a, b)
+
+
+def _axis_amplitudes(geometry, eta, focal, aperture, windows):
+    """Largest on-axis |q1 - 1| / A at each axial position z of `windows`
+    ({z: (t_from, t_to)}) over its time window, driven on x1 = 0 by the
+    one-sided turn-on of eq. hifuBC (small amplitude, no dissipation), in the
+    Cartesian form (geometry 0) or the axisymmetric (z, r) form (1)."""
+    amp = 1e-6
+    zmax = max(windows)
+    nz, nr = int(round((zmax + 1.0) * eta)), int(round((aperture + 3.0) * eta))
+    p = Params(nx=nz, ny=nr, bc=(oracle.BC_HIFU, BC_EXTRAP, oracle.BC_REFLECT, BC_EXTRAP),
+               geometry=geometry, beta=3.5, delta=0.0, dx=1.0 / eta, nu_w=0.4, amp=amp,
+               focal=focal, aperture=aperture, envelope=0,
+               t0=-aperture * aperture / (2.0 * focal) - 0.1)
+    o = oracle.Oracle(p, wl.ambient(nz, nr))
+    top = {z: 0.0 for z in windows}
+    t_end = max(w[1] for w in windows.values())
+    o.run(10 ** 7, min(w[0] for w in windows.values()))
+    while o.scalars()["t"] < t_end:
+        o.run(1, t_end)
+        t = o.scalars()["t"]
+        q1 = o.q()[0, 0]
+        for z, (a, b) in windows.items():
+            if a <= t <= b:
+                top[z] = max(top[z], abs(q1[int(z * eta)] - 1.0))
+    o.close()
+    return {z: v / amp for z, v in top.items()}
+
+
+def test_axisymmetric_drive_converges_spherically():
+    """In the (z, r) form the drive of eq. hifuBC is a spherical cap converging
+    on (F, 0); in the Cartesian form the same drive is a cylindrical one.  A
+    converging spherical wave's amplitude grows as F / (F - d), a cylindrical
+    one's as sqrt(F / (F - d)), so between two axial points the axisymmetric
+    gain exceeds the Cartesian gain by sqrt((F - z1) / (F - z2)); the
+    scheme's own damping, the same in both forms, cancels in that ratio.  The
+    windows tau = t - z in [6, 8.5] see the direct wave at full turn-on and
+    end before the wave from the rim of the aperture (F = 60, a = 20
+    wavelengths) reaches the axis."""
+    F, a, z1, z2 = 60.0, 20.0, 0.5, 10.0
+    win = {z1: (z1 + 6.0, z1 + 8.5), z2: (z2 + 6.0, z2 + 8.5)}
+    cart = _axis_amplitudes(0, 20.0, F, a, win)
+    axi = _axis_amplitudes(1, 20.0, F, a, win)
+    extra = (axi[z2] / axi[z1]) / (cart[z2] / cart[z1])
+    expect = np.sqrt((F - z1) / (F - z2))
+    assert abs(extra / expect - 1.0) < 0.003, (extra, expect, cart, axi)
+
+
 # ---------------------------------------------------------------- axisymmetric
 
 def test_axisymmetric_source_terms_exact():
