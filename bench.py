@@ -73,6 +73,11 @@ def parse():
                     help="FP32 cell update as written instead of the compensated sum")
     ap.add_argument("--flush-mb", type=int, default=512,
                     help="L2 flush buffer written before every timed step (0: none)")
+    ap.add_argument("--record-traffic", metavar="CSV",
+                    help="write the DRAM traffic per sweep launch from an ncu CSV capture "
+                         "(dram__bytes_read.sum, dram__bytes_write.sum, --print-units base) "
+                         "keyed to the current kernel sources, then exit (no GPU needed)")
+    ap.add_argument("--traffic-out", default=os.path.join(ROOT, "profiles", "ncu_traffic.json"))
     return ap.parse_args()
 
 
@@ -222,6 +227,60 @@ def ncu_traffic(kernel_key: str):
     if not e or e.get("source_digest") != source_digest():
         return None
     return e.get("dram_bytes_per_launch")
+
+
+# sweep kernels of the timed step, by the demangled names ncu prints: the
+# binary32 x2 sweep's second kernel (REDO = true) belongs to the x2 sweep
+_TRAFFIC_KEYS = [
+    (r"k_sweep_x32<", "k_sweep_x_fp32"),
+    (r"k_sweep_y32<", "k_sweep_y_fp32"),
+    (r"k_sweep_x<fvna::P64", "k_sweep_x_fp64"),
+    (r"k_sweep_y<fvna::P64", "k_sweep_y_fp64"),
+]
+
+
+def record_traffic(csv_path: str, out_path: str, n: int = N_SIDE) -> dict:
+    """DRAM bytes per launch of each sweep from an ncu CSV capture of
+    `bench.py` on the n x n pulse, keyed to the digest of the kernel sources
+    this script sees (a capture taken on other sources is never matched)."""
+    import csv
+    import re
+    rows = [r for r in csv.reader(open(csv_path)) if r]
+    hdr_i = next(i for i, r in enumerate(rows) if "Metric Name" in r and "Kernel Name" in r)
+    hdr = rows[hdr_i]
+    ci = {k: hdr.index(k) for k in ("ID", "Kernel Name", "Metric Name", "Metric Unit",
+                                     "Metric Value")}
+    per_launch = {}
+    for r in rows[hdr_i + 1:]:
+        if len(r) < len(hdr) or r[ci["Metric Name"]] not in ("dram__bytes_read.sum",
+                                                            "dram__bytes_write.sum"):
+            continue
+        unit = r[ci["Metric Unit"]]
+        if unit not in ("byte", "bytes", "B"):
+            raise ValueError(f"unit {unit!r}: capture with --print-units base")
+        v = float(r[ci["Metric Value"]].replace(",", ""))
+        key = (int(r[ci["ID"]]), r[ci["Kernel Name"]])
+        per_launch[key] = per_launch.get(key, 0.0) + v
+    out = {"_note": ("dram__bytes_read.sum + dram__bytes_write.sum per launch, averaged over "
+                     "the captured launches, from " + os.path.basename(csv_path) + "; valid "
+                     "while the kernel sources hash to source_digest (written by bench.py "
+                     "--record-traffic, never by hand)")}
+    digest = source_digest()
+    for pat, key in _TRAFFIC_KEYS:
+        # launches in capture order; the x2 sweep's second kernel follows its first
+        ids = [k for k in per_launch if re.search(pat, k[1])]
+        tot = sum(per_launch[k] for k in ids)
+        # k_sweep_y32<LIM, COMP, REDO>: one launch of each per step
+        firsts = [k for k in ids if key != "k_sweep_y_fp32" or re.search(r",\s*false>\(", k[1])]
+        launches = len(firsts)
+        if launches == 0:
+            continue
+        out[f"{key}_{n}x{n}"] = {"dram_bytes_per_launch": int(round(tot / launches)),
+                                 "launches": launches, "source_digest": digest}
+    with open(out_path, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    return out
 
 
 def peaks():
@@ -709,6 +768,9 @@ def run_netfwd(args):
 
 def main():
     args = parse()
+    if args.record_traffic:
+        print(json.dumps(record_traffic(args.record_traffic, args.traffic_out, args.n)))
+        return 0
     if args.workload == "netfwd":
         return run_netfwd(args)
     if args.workload == "learned":

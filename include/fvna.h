@@ -100,7 +100,11 @@ typedef struct fvna_config {
   int compensated;      /* FVNA_FP32_PERT: 1 = sum each cell update with error-free
                            two-sums (one final rounding), 0 = as written */
   int splitting;        /* enum fvna_splitting */
-  int reserved;         /* 0 */
+  int wait_limit;       /* FVNA_FP32_PERT: polls a sweep kernel makes while it waits for one of
+                           its own asynchronous tile copies before it gives up (the run then
+                           stops with FVNA_ERR_TIMEOUT and the context stays usable); 0 = the
+                           default (2^22 polls, a few seconds at most); a negative value gives
+                           up before the first poll, to exercise that error path */
 } fvna_config;
 
 /* One domain.  Coordinates are those of the lower-left corner of cell (0,0);
@@ -275,8 +279,8 @@ int fvna_riemann(int precision, double beta, int n, const double *qL, const doub
  *             described at the top of this file (caller-owned, read only)
  *   q_out     device pointer, same layout (caller-owned); may equal q_in
  *   t, dt     time of the state and the step to take (driven borders use t)
- *   smax_out  host pointer or NULL: receives max|s| of the step, for the
- *             caller's own CFL rule (section 4)
+ *   smax_out  host pointer or NULL: receives max|s| of the step, from which
+ *             the caller picks its next dt
  *   stream    cudaStream_t to run on (NULL = legacy default stream)
  * The intermediate planes and bookkeeping live in one file-scope device array
  * of about 13 MB, which every GPU that loads this library keeps until the
@@ -285,9 +289,12 @@ int fvna_riemann(int precision, double beta, int n, const double *qL, const doub
  * blocks until its step is done.  All calls share the array and each call
  * clears what must start at zero, but calls that overlap on the GPU (two host
  * threads, or several streams) race on it.  Results equal those of
- * fvna_step with cfg->dt_fixed = dt.  Returns FVNA_OK, FVNA_ERR_ARG (also for
- * cfg->splitting other than FVNA_SPLIT_GODUNOV), FVNA_ERR_SIZE for a larger domain, FVNA_ERR_NONREAL / FVNA_ERR_NAN from the
- * step, or FVNA_ERR_CUDA. */
+ * fvna_step with cfg->dt_fixed = dt, bit for bit.  The library cannot check
+ * the type or size of the caller's buffers: they must hold 3*nx*ny binary64
+ * values each on the current device.  Returns FVNA_OK, FVNA_ERR_ARG (the
+ * checks of fvna_init, a non-finite t or dt, or cfg->splitting other than
+ * FVNA_SPLIT_GODUNOV), FVNA_ERR_SIZE for a larger domain, FVNA_ERR_NONREAL /
+ * FVNA_ERR_NAN from the step, or FVNA_ERR_CUDA. */
 #define FVNA_NOALLOC_MAX_CELLS 524288
 int fvna_step_noalloc(const fvna_config *cfg, const fvna_domain *dom, const double *q_in,
                       double *q_out, double t, double dt, double *smax_out, void *stream);

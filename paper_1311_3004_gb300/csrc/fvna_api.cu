@@ -503,6 +503,7 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   a.limiter = cfg->limiter; a.geometry = cfg->geometry; a.sweeps = cfg->sweeps;
   a.tile_y = c->tile_y;
   a.compensated = comp;
+  a.wait_polls = cfg->wait_limit == 0 ? (1 << 22) : cfg->wait_limit < 0 ? 0 : cfg->wait_limit;
   a.tmaps = c->d_maps;
   a.counters = c->d_ctr;
   a.redo = c->d_redo;

@@ -99,10 +99,16 @@ extern "C" int fvna_step_noalloc(const fvna_config *cfg, const fvna_domain *dom,
   if (cfg->precision != FVNA_FP64) return FVNA_ERR_ARG;
   if (cfg->geometry != FVNA_CARTESIAN && cfg->geometry != FVNA_AXISYMMETRIC) return FVNA_ERR_ARG;
   if (cfg->limiter < FVNA_LIM_MC || cfg->limiter > FVNA_LIM_LW) return FVNA_ERR_ARG;
-  if (cfg->sweeps < 0 || cfg->sweeps > 7 || !(cfg->dx > 0.0) || !(dt > 0.0)) return FVNA_ERR_ARG;
+  if (cfg->sweeps < 0 || cfg->sweeps > 7) return FVNA_ERR_ARG;
+  // the same parameter checks as fvna_init, plus a finite time and step
+  if (!(cfg->dx > 0.0) || !std::isfinite(cfg->dx)) return FVNA_ERR_ARG;
+  if (!std::isfinite(cfg->beta) || !(cfg->delta >= 0.0) || !std::isfinite(cfg->delta))
+    return FVNA_ERR_ARG;
+  if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(t)) return FVNA_ERR_ARG;
   if (cfg->splitting != FVNA_SPLIT_GODUNOV) return FVNA_ERR_ARG;   // takes the Godunov step
   const int nx = dom->nx, ny = dom->ny;
   if (nx < 1 || ny < 1) return FVNA_ERR_ARG;
+  if (dom->bc[0] == FVNA_BC_HIFU && !(dom->focal > 0.0)) return FVNA_ERR_ARG;
   for (int s = 0; s < 4; s++) {
     if (dom->bc[s] < FVNA_BC_PERIODIC || dom->bc[s] > FVNA_BC_HIFU) return FVNA_ERR_ARG;
     int len = s < 2 ? nx : ny;

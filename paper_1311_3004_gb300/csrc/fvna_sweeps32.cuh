@@ -194,7 +194,8 @@ __device__ __forceinline__ int take_tile_collect(unsigned t) {
   return (int)__shfl_sync(0xffffffffu, t, 0);
 }
 
-// error exit of a failed wait: flag the domain, let the copy land, stop
+// error exit of a failed wait: flag the domain, let the copy land (default
+// limit, whatever the first wait's was), stop
 __device__ __forceinline__ void wait_failed(DomScal *S, uint64_t *bar, unsigned parity, int lane) {
   if (lane == 0) atomicOr(&S->status_bits, ST_TIMEOUT);
   mbar_wait(bar, parity);
@@ -427,7 +428,7 @@ __global__ void __launch_bounds__(32, X32_MINBLOCKS) k_sweep_x32(StepArgs A) {
       bulk_wait_read();  // the previous tile's stores have read the buffers
       load(M, x0, y0);
     }
-    bool ok = __all_sync(0xffffffffu, mbar_wait(bar, phase));
+    bool ok = __all_sync(0xffffffffu, mbar_wait(bar, phase, A.wait_polls));
     if (!ok) {
       wait_failed(S, bar, phase, lane);
       break;
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(32, X32_MINBLOCKS) k_sweep_x32(StepArgs A) {
         // the march wrote into the tile: load it again, general split
         __syncwarp();
         if (lane == 0) load(M, x0, y0);
-        if (!__all_sync(0xffffffffu, mbar_wait(bar, phase))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(bar, phase, A.wait_polls))) {
           wait_failed(S, bar, phase, lane);
           break;
         }
@@ -676,7 +677,7 @@ __device__ __forceinline__ int y32_tile(const StepArgs &A, const DomDev &D, DomS
   for (int c = 0; c < nch; c++) {
     unsigned s = (base + c) % Y32_STAGES;
     unsigned par = ((base + c) / Y32_STAGES) & 1u;
-    if (!__all_sync(0xffffffffu, mbar_wait(&bars[s], par))) {
+    if (!__all_sync(0xffffffffu, mbar_wait(&bars[s], par, A.wait_polls))) {
       wait_failed(S, &bars[s], par, lane);
       // the remaining chunks of this tile that were issued still land
       for (int d = c + 1; d < nch && d < c + Y32_STAGES; d++) {

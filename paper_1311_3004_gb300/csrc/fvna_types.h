@@ -81,6 +81,8 @@ struct StepArgs {
   int redo_off;
   int fold_advance;              // binary32 x2 sweep: its last block ends the step
                                  // (k_advance's work; arrivals counted in counters[2])
+  int wait_polls;                // binary32 sweeps: polls of a first wait for a tile copy
+                                 // before giving up (0: give up at once)
 };
 
 }  // namespace fvna

@@ -83,12 +83,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for a phase of `bar`.  Every try_wait may suspend the thread
-// for a while, so the limit is a few seconds at most; false means the copy
-// never arrived (the caller records an error and stops using the buffer).
+// Bounded wait for a phase of `bar`: at most `limit` polls.  Every try_wait
+// may suspend the thread for a while, so the default limit is a few seconds
+// at most; false means the copy did not arrive in time (the caller records
+// an error, waits once more with the default limit for the copy to land, and
+// stops using the buffer).
 constexpr int WAIT_LIMIT = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-  for (int i = 0; i < WAIT_LIMIT; i++)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity,
+                                          int limit = WAIT_LIMIT) {
+  for (int i = 0; i < limit; i++)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

@@ -47,7 +47,7 @@ class Config(ctypes.Structure):
                 ("nu_w", ctypes.c_double), ("nu_max", ctypes.c_double),
                 ("dt_fixed", ctypes.c_double), ("steps_per_graph", ctypes.c_int),
                 ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("compensated", ctypes.c_int),
-                ("splitting", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("splitting", ctypes.c_int), ("wait_limit", ctypes.c_int)]
 
 
 class Domain(ctypes.Structure):
@@ -167,9 +167,9 @@ def _check(rc: int, where: str) -> int:
 
 def make_config(precision=FP64, geometry=CARTESIAN, limiter=LIM_MC, sweeps=7, beta=3.5,
                 delta=0.0, dx=1.0, nu_w=0.9, nu_max=1.0, dt_fixed=0.0, steps_per_graph=0,
-                tile_x=0, tile_y=0, compensated=1, splitting=0) -> Config:
+                tile_x=0, tile_y=0, compensated=1, splitting=0, wait_limit=0) -> Config:
     return Config(precision, geometry, limiter, sweeps, beta, delta, dx, nu_w, nu_max, dt_fixed,
-                  steps_per_graph, tile_x, tile_y, compensated, splitting, 0)
+                  steps_per_graph, tile_x, tile_y, compensated, splitting, wait_limit)
 
 
 def make_domain(nx, ny, bc=(BC_EXTRAP,) * 4, envelope=0, x0=0.0, y0=0.0, t0=0.0, dt0=0.0,
@@ -460,12 +460,34 @@ def net_params_dict(flat: np.ndarray) -> dict:
     return out
 
 
+def _check_noalloc_buffers(domain: Domain, *bufs) -> None:
+    import torch
+    n = 3 * int(domain.nx) * int(domain.ny)
+    for b in bufs:
+        if not isinstance(b, torch.Tensor):
+            raise FvnaError(ERR_ARG, "step_noalloc: buffers must be torch tensors")
+        if b.dtype != torch.float64:
+            raise FvnaError(ERR_ARG, f"step_noalloc: buffer dtype {b.dtype}, expected float64")
+        if not b.is_contiguous():
+            raise FvnaError(ERR_ARG, "step_noalloc: buffer is not contiguous")
+        if b.numel() != n:
+            raise FvnaError(ERR_ARG, f"step_noalloc: buffer holds {b.numel()} values, the "
+                                     f"domain needs 3*nx*ny = {n}")
+        if not b.is_cuda or b.device.index != torch.cuda.current_device():
+            raise FvnaError(ERR_ARG, f"step_noalloc: buffer on {b.device}, expected the "
+                                     "current CUDA device")
+
+
 def step_noalloc(config: Config, domain: Domain, q_in, q_out, t: float, dt: float,
                  stream=None):
     """One binary64 step that allocates nothing (fvna_step_noalloc).
 
     q_in, q_out: torch CUDA float64 tensors of shape (3, ny, nx) owned by the
-    caller (they may be the same tensor).  Returns (status, max|s|)."""
+    caller (they may be the same tensor).  Returns (status, max|s|).  The C
+    entry point takes bare device pointers and cannot see a buffer's type or
+    size, so a wrong tensor is refused here (FvnaError, ERR_ARG) before
+    anything is launched."""
+    _check_noalloc_buffers(domain, q_in, q_out)
     if stream is None:
         stream = _current_stream()
     sm = ctypes.c_double(0.0)

@@ -133,3 +133,21 @@ def test_argument_errors_before_device_work(lib):
     for code in [0, -1, -2, -3, -4, -5, -6, -7]:
         assert lib.fvna_strerror(code)
     assert b"unknown" in lib.fvna_strerror(-99)
+
+
+def test_step_noalloc_refuses_wrong_buffers_before_any_launch(lib):
+    """fvna_step_noalloc takes bare device pointers, so the binding checks the
+    buffers' type, layout and size itself and raises before the C call."""
+    torch = pytest.importorskip("torch")
+    cfg = fvna.make_config(precision=fvna.FP64, dx=0.1, dt_fixed=0.01)
+    dom = fvna.make_domain(8, 5)
+    good = torch.zeros((3, 5, 8), dtype=torch.float64)
+    bad = [torch.zeros((3, 5, 8), dtype=torch.float32),              # binary32
+           torch.zeros((3, 5, 7), dtype=torch.float64),              # too small
+           torch.zeros((3, 8, 5), dtype=torch.float64).transpose(1, 2),  # not contiguous
+           good.numpy(),                                             # not a tensor
+           good]                                                     # host memory
+    for b in bad:
+        with pytest.raises(fvna.FvnaError) as e:
+            fvna.step_noalloc(cfg, dom, b, b, 0.0, 0.01)
+        assert e.value.code == fvna.ERR_ARG

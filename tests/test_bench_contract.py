@@ -25,3 +25,36 @@ def test_reference_arm_prints_one_contract_line():
     assert d["config"]["workload"] == "gaussian_pulse_2048x2048"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_traffic_record_is_keyed_to_the_sources(tmp_path):
+    """bench.py --record-traffic sums DRAM reads and writes per launch from an
+    ncu CSV (the x2 sweep's second kernel counted with its first) and keys them
+    to the digest of the kernel sources, so a stale capture is never used."""
+    sys.path.insert(0, ROOT)
+    import bench
+    hdr = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream",'
+           '"Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit",'
+           '"Metric Value"')
+    def row(i, name, metric, v):
+        return (f'"{i}","1","python","h","{name}","1","7","(32, 1, 1)","(9, 1, 1)","0","10.3",'
+                f'"Command line profiler metrics","{metric}","byte","{v}"')
+    x = "void fvna::k_sweep_x32<32, 0, true>(fvna::StepArgs)"
+    y1 = "void fvna::k_sweep_y32<0, true, false>(fvna::StepArgs)"
+    y2 = "void fvna::k_sweep_y32<0, true, true>(fvna::StepArgs)"
+    lines = ["==PROF== Connected", hdr]
+    for s in range(2):
+        b = 10 * s
+        lines += [row(b, x, "dram__bytes_read.sum", "50,000,000"),
+                  row(b, x, "dram__bytes_write.sum", 6000000 + s * 2),
+                  row(b + 1, y1, "dram__bytes_read.sum", 30000000),
+                  row(b + 1, y1, "dram__bytes_write.sum", 20000000),
+                  row(b + 2, y2, "dram__bytes_read.sum", 1000)]
+    csv_path = tmp_path / "t.csv"
+    csv_path.write_text("\n".join(lines) + "\n")
+    out = bench.record_traffic(str(csv_path), str(tmp_path / "t.json"))
+    assert out["k_sweep_x_fp32_2048x2048"]["dram_bytes_per_launch"] == 56000001
+    assert out["k_sweep_y_fp32_2048x2048"]["dram_bytes_per_launch"] == 50001000
+    assert out["k_sweep_y_fp32_2048x2048"]["launches"] == 2
+    assert out["k_sweep_x_fp32_2048x2048"]["source_digest"] == bench.source_digest()
+    assert json.loads((tmp_path / "t.json").read_text()) == out
