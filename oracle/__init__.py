@@ -4,9 +4,10 @@ TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg are the only callers.  The GPU library never
 imports or calls anything here, and this package imports nothing from it.
 
-The arithmetic lives in ``fvna_oracle.c`` (plain C, binary64,
-``-ffp-contract=off``); this module compiles it with gcc and wraps it with
-ctypes.  See the header of ``fvna_oracle.c`` for what each function follows in
+The arithmetic lives in ``fvna_oracle.c`` (the paper's 2D scheme) and
+``fvna_oracle3d.c`` (its three-dimensional form), plain C, binary64,
+``-ffp-contract=off``; this module compiles them with gcc and wraps them with
+ctypes.  See the headers of the C files for what each function follows in
 the paper.
 """
 from __future__ import annotations
@@ -20,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fvna_oracle.c")
+_SRC3 = os.path.join(_HERE, "fvna_oracle3d.c")
 _LIB = os.path.join(_HERE, "_build", "libfvna_oracle.so")
 
 BC_PERIODIC, BC_EXTRAP, BC_REFLECT, BC_TAYLOR, BC_HIFU = 0, 1, 2, 3, 4
@@ -30,10 +32,12 @@ ST_NONREAL, ST_CFL, ST_NAN = 1, 2, 4
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (binary64, no FP contraction)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    srcs = [_SRC, _SRC3]
+    if force or not os.path.exists(_LIB) or \
+            os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in srcs):
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+                               "-fPIC", "-shared", "-o", tmp, *srcs, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -49,6 +53,14 @@ class _Params(ctypes.Structure):
                 ("taylor_angle", ctypes.c_double), ("amp", ctypes.c_double),
                 ("focal", ctypes.c_double), ("aperture", ctypes.c_double),
                 ("splitting", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class _Params3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("bc", ctypes.c_int * 6), ("limiter", ctypes.c_int), ("sweeps", ctypes.c_int),
+                ("beta", ctypes.c_double), ("delta", ctypes.c_double), ("dx", ctypes.c_double),
+                ("nu_w", ctypes.c_double), ("nu_max", ctypes.c_double),
+                ("dt_fixed", ctypes.c_double), ("t0", ctypes.c_double)]
 
 
 _lib = None
@@ -76,6 +88,15 @@ def lib():
                                 ctypes.c_double, dp]
         L.ora_limiter.restype = ctypes.c_double
         L.ora_limiter.argtypes = [ctypes.c_int, ctypes.c_double]
+        L.ora3_create.restype = ctypes.c_void_p
+        L.ora3_create.argtypes = [ctypes.POINTER(_Params3), dp]
+        L.ora3_destroy.argtypes = [ctypes.c_void_p]
+        L.ora3_run.restype = ctypes.c_long
+        L.ora3_run.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_long]
+        L.ora3_get.argtypes = [ctypes.c_void_p, dp]
+        L.ora3_scalars.argtypes = [ctypes.c_void_p, dp]
+        L.ora3_interface.restype = ctypes.c_int
+        L.ora3_interface.argtypes = [ctypes.c_double, dp, dp, dp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -235,3 +256,91 @@ def run(params: Params, q0: np.ndarray, steps: int, t_end: float = -np.inf):
     q, sc = o.q(), o.scalars()
     o.close()
     return q, sc
+
+
+# ---------------------------------------------------------------- three dimensions
+
+@dataclass
+class Params3:
+    """One 3D run's parameters (fvna_oracle3d.c).  sweeps: bit 0 x1, bit 1 x2,
+    bit 2 x3, bit 3 source; bc: x1-low, x1-high, x2-low, x2-high, x3-low,
+    x3-high, each periodic, extrapolation or reflective."""
+    nx: int
+    ny: int
+    nz: int
+    bc: tuple = (BC_EXTRAP,) * 6
+    limiter: int = LIM_MC
+    sweeps: int = 15
+    beta: float = 3.5
+    delta: float = 0.0
+    dx: float = 1.0
+    nu_w: float = 0.9
+    nu_max: float = 1.0
+    dt_fixed: float = 0.0
+    t0: float = 0.0
+
+    def to_c(self) -> _Params3:
+        p = _Params3()
+        for name, _ in _Params3._fields_:
+            if name == "bc":
+                p.bc = (ctypes.c_int * 6)(*self.bc)
+            else:
+                setattr(p, name, getattr(self, name))
+        return p
+
+
+class Oracle3:
+    """A running 3D oracle state.  q0 has shape (4, nz, ny, nx), total variables."""
+
+    def __init__(self, params: Params3, q0: np.ndarray):
+        q0 = np.ascontiguousarray(q0, dtype=np.float64)
+        assert q0.shape == (4, params.nz, params.ny, params.nx)
+        self.params = params
+        self._p = params.to_c()
+        self._h = lib().ora3_create(ctypes.byref(self._p), _dptr(q0))
+
+    def run(self, steps: int, t_end: float = -np.inf) -> int:
+        t_end = float(t_end) if np.isfinite(t_end) else -1e300
+        return int(lib().ora3_run(self._h, t_end, int(steps)))
+
+    def q(self) -> np.ndarray:
+        p = self.params
+        out = np.empty((4, p.nz, p.ny, p.nx), dtype=np.float64)
+        lib().ora3_get(self._h, _dptr(out))
+        return out
+
+    def scalars(self) -> dict:
+        out = np.zeros(6, dtype=np.float64)
+        lib().ora3_scalars(self._h, _dptr(out))
+        d = dict(zip(["t", "dt", "smax", "step", "status", "dt_last"], out.tolist()))
+        d["step"] = int(d["step"])
+        d["status"] = int(d["status"])
+        return d
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ora3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def run3(params: Params3, q0: np.ndarray, steps: int, t_end: float = -np.inf):
+    """Convenience: run a 3D state and return (q, scalars)."""
+    o = Oracle3(params, q0)
+    o.run(steps, t_end)
+    q, sc = o.q(), o.scalars()
+    o.close()
+    return q, sc
+
+
+def interface3(beta: float, qL, qR):
+    """One x1 interface of the 3D solver: (s[4], W[4,4] rows = families, amdq[4],
+    apdq[4], nonreal)."""
+    qL = np.ascontiguousarray(qL, dtype=np.float64)
+    qR = np.ascontiguousarray(qR, dtype=np.float64)
+    s, W, am, ap = np.zeros(4), np.zeros(16), np.zeros(4), np.zeros(4)
+    nr = lib().ora3_interface(beta, _dptr(qL), _dptr(qR), _dptr(s), _dptr(W), _dptr(am),
+                              _dptr(ap))
+    return s, W.reshape(4, 4), am, ap, bool(nr)
