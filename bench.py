@@ -57,9 +57,16 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=["gaussian", "plane", "focused", "batched", "learned",
-                                           "netfwd", "taylor", "hifu"],
+                                           "netfwd", "taylor", "hifu", "gaussian3d"],
                     default="gaussian",
                     help="gaussian: the headline line; the others print their own line")
+    ap.add_argument("--n3", type=int, default=256, help="side of the 3D pulse workload")
+    ap.add_argument("--taylor-extent", type=float, default=12.0,
+                    help="side of the square window of the rotated Taylor shocks (units of x)")
+    ap.add_argument("--taylor-angles", default="0,32,16,8,4",
+                    help="theta_T = pi/k for these k (0: theta_T = 0)")
+    ap.add_argument("--taylor-etas", default="5,10,20,41,82")
+    ap.add_argument("--taylor-nus", default="0.6,0.7,0.8,0.9,0.99")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile-x", type=int, default=0,
                     help="x1-sweep tile width (16/32/64; 0: the library's choice)")
@@ -206,16 +213,26 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- native
 
-def source_digest():
+# the sources the 2D step's kernels, their launch shapes and tile lists are
+# built from (the 3D, network and allocation-free units do not enter)
+_SWEEP_SOURCES = ["fvna_api.cu", "fvna_device.cuh", "fvna_fp32.cu", "fvna_fp64.cu",
+                  "fvna_launch.h", "fvna_precision.inc", "fvna_step.cuh", "fvna_sweeps.cuh",
+                  "fvna_sweeps32.cuh", "fvna_types.h", "fvna_x2.cuh"]
+
+
+_SWEEP3_SOURCES = ["fvna_3d.cuh", "fvna_3d.inc", "fvna_3d32.cu", "fvna_3d64.cu", "fvna_api3d.cu",
+                   "fvna_launch3.h"]
+
+
+def source_digest(files=None):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1311_3004_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".inc")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in sorted(files or _SWEEP_SOURCES):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_key: str):
+def ncu_traffic(kernel_key: str, files=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel sources; otherwise None."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -224,18 +241,19 @@ def ncu_traffic(kernel_key: str):
     except Exception:
         return None
     e = d.get(kernel_key)
-    if not e or e.get("source_digest") != source_digest():
+    if not e or e.get("source_digest") != source_digest(files):
         return None
     return e.get("dram_bytes_per_launch")
 
 
 # sweep kernels of the timed step, by the demangled names ncu prints: the
 # binary32 x2 sweep's second kernel (REDO = true) belongs to the x2 sweep
+# (ncu prints template arguments without namespaces and bools as 0 / 1)
 _TRAFFIC_KEYS = [
     (r"k_sweep_x32<", "k_sweep_x_fp32"),
     (r"k_sweep_y32<", "k_sweep_y_fp32"),
-    (r"k_sweep_x<fvna::P64", "k_sweep_x_fp64"),
-    (r"k_sweep_y<fvna::P64", "k_sweep_y_fp64"),
+    (r"k_sweep_x<(fvna::)?P64", "k_sweep_x_fp64"),
+    (r"k_sweep_y<(fvna::)?P64", "k_sweep_y_fp64"),
 ]
 
 
@@ -271,7 +289,8 @@ def record_traffic(csv_path: str, out_path: str, n: int = N_SIDE) -> dict:
         ids = [k for k in per_launch if re.search(pat, k[1])]
         tot = sum(per_launch[k] for k in ids)
         # k_sweep_y32<LIM, COMP, REDO>: one launch of each per step
-        firsts = [k for k in ids if key != "k_sweep_y_fp32" or re.search(r",\s*false>\(", k[1])]
+        firsts = [k for k in ids
+                  if key != "k_sweep_y_fp32" or re.search(r",\s*(false|0)>\(", k[1])]
         launches = len(firsts)
         if launches == 0:
             continue
@@ -519,10 +538,11 @@ def run_taylor(args):
     torch, fvna = _setup_cuda()
     from paper_1311_3004_gb300 import analysis
     ratio, beta, T = 1e-7, 3.5, 100.0
-    etas = [5, 10, 20, 41, 82]
-    nus = [0.6, 0.7, 0.8, 0.9, 0.99]
-    table, cell_updates, total_s = {}, 0.0, 0.0
-    for k in (0, 32, 16, 8, 4):
+    etas = [int(e) for e in args.taylor_etas.split(",")]
+    nus = [float(v) for v in args.taylor_nus.split(",")]
+    ext = float(args.taylor_extent)
+    table, cell_updates, total_s, runs = {}, 0.0, 0.0, []
+    for k in (int(a) for a in args.taylor_angles.split(",")):
         angle = 0.0 if k == 0 else np.pi / k
         rows = {"E1": [], "Einf": []}
         for nu in nus:
@@ -532,8 +552,8 @@ def run_taylor(args):
                 if k == 0:
                     nx, ny, x0, y0, bc = int(round(30.0 * eta)), 4, -15.0, 0.0, (3, 3, 0, 0)
                 else:
-                    nx = ny = int(round(12.0 * eta))
-                    x0 = y0 = -6.0
+                    nx = ny = int(round(ext * eta))
+                    x0 = y0 = -0.5 * ext
                     bc = (3, 3, 3, 3)
                 q0 = wl.taylor_initial(nx, ny, dx, ratio, x0=x0, y0=y0, angle=angle)
                 cfg = fvna.make_config(precision=fvna.FP64, beta=beta, delta=ratio * beta, dx=dx,
@@ -548,9 +568,13 @@ def run_taylor(args):
                 e1, ei = analysis.taylor_line_errors(q, cx, cy, dx, T, angle, ratio)
                 e1s.append(e1)
                 eis.append(ei)
+                runs.append({"k": k, "nu": nu, "eta": eta, "E1": e1, "Einf": ei, "s": sec})
                 cell_updates += nx * ny * st["steps"]
                 total_s += sec
             for name, e in (("E1", e1s), ("Einf", eis)):
+                if len(etas) < 2:
+                    rows[name].append((float("nan"), float("nan"), e[-1]))
+                    continue
                 fit = np.polyfit(np.log(etas), np.log(e), 1)
                 pred = np.polyval(fit, np.log(etas))
                 r2 = 1.0 - np.sum((np.log(e) - pred) ** 2) / np.sum(
@@ -564,7 +588,9 @@ def run_taylor(args):
                       for n, v in rows.items()}
     print(json.dumps({"metric": METRIC, "value": cell_updates / total_s, "unit": METRIC,
                       "workload": "taylor_shock_study_moving_window", "dtype": "f64",
-                      "cell_updates": cell_updates, "time_s": total_s, "table": table}),
+                      "window_extent": ext, "etas": etas, "nus": nus,
+                      "cell_updates": cell_updates, "time_s": total_s, "table": table,
+                      "runs": runs}),
           flush=True)
     return 0
 
@@ -701,6 +727,73 @@ def run_batched(args):
     return 0
 
 
+def run_gaussian3d(args):
+    """The 3D form (fvna3_*): the n^3 pulse (256^3 unless --n3), one bench step
+    = one full 3D time step (three sweeps, source, dt update), L2 flushed
+    before every timed step, device times from CUDA events per kernel."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1311_3004_gb300 import fvna
+    n = args.n3
+    w = wl.gaussian3d(n)
+    cells = n ** 3
+    flush = torch.empty(max(1, args.flush_mb) * 1024 * 1024 // 4, dtype=torch.float32,
+                        device="cuda")
+    pk, pk_kind = peaks()
+    out = {}
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for prec, name, steps in ((fvna.FP32_PERT, "fp32", args.steps),
+                                  (fvna.FP64, "fp64", max(3, args.steps // 10))):
+            cfg = fvna.make_config(precision=prec, beta=w["beta"], delta=w["delta"], dx=w["dx"],
+                                   nu_w=w["nu_w"],
+                                   compensated=0 if args.plain_update else 1)
+            s = fvna.Solver3(cfg, fvna.make_domain3(n, n, n, w["bc"]), w["q0"])
+            for _ in range(args.warmup):
+                if args.flush_mb > 0:
+                    flush.fill_(1.0)
+                s.step_timed()
+            n0 = s.launch_count()
+            per = []
+            for _ in range(steps):
+                if args.flush_mb > 0:
+                    flush.fill_(1.0)
+                per.append(s.step_timed())
+            launches = s.launch_count() - n0
+            s.close()
+            per = np.array(per)
+            esz = 4 if prec == fvna.FP32_PERT else 8
+            alg = 2 * 4 * esz * cells            # one sweep reads and writes the four fields
+            kn = ["k3_sweep_x", "k3_sweep_v (x2)", "k3_sweep_v (x3)", "k3_source"]
+            avg = per[:, :4].mean(axis=0)
+            k = int(np.argmax(avg))
+            ach = alg / (avg[k] * 1e-3) / 1e9
+            out[name] = {"value": cells * steps / (per.sum() / 1e3),
+                         "ms_per_step": float(per.sum(axis=1).mean()),
+                         "kernel_ms": {kn[i]: float(avg[i]) for i in range(4)} |
+                                      {"k3_advance": float(per[:, 4].mean())},
+                         "gpu_launches": int(launches),
+                         "roofline": {"bound": "hbm", "kernel": kn[k], "achieved": ach,
+                                      "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                      "frac": ach / pk["hbm_gbs"], "peak_source": pk_kind,
+                                      "algorithmic_bytes_per_launch": alg,
+                                      "traffic": ncu_traffic(f"{kn[k].split()[0]}_{name}_{n}",
+                                                             _SWEEP3_SOURCES)},
+                         "step_fraction": alg / 2 / (per.sum(axis=1).mean() * 1e-3) / 1e9 /
+                         pk["hbm_gbs"]}
+    line = {"metric": METRIC, "value": out["fp32"]["value"], "unit": METRIC, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["fp32"]["ms_per_step"], "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "cells": cells, "precision": "fp32",
+                       "l2": f"flushed before every timed step ({args.flush_mb} MB write)"},
+            "fp32": out["fp32"], "fp64": out["fp64"], "roofline": out["fp32"]["roofline"],
+            "gpu_launches": out["fp32"]["gpu_launches"], "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_learned(args):
     """Coarse (2048x512) focused-source runs with the learned correction
     against the plain fine-grid (4096x1024) FP64 solver: training data from
@@ -787,6 +880,8 @@ def main():
         return run_taylor(args)
     if args.workload == "hifu":
         return run_hifu(args)
+    if args.workload == "gaussian3d":
+        return run_gaussian3d(args)
     return run_native(args)
 
 

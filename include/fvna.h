@@ -299,6 +299,67 @@ int fvna_riemann(int precision, double beta, int n, const double *qL, const doub
 int fvna_step_noalloc(const fvna_config *cfg, const fvna_domain *dom, const double *q_in,
                       double *q_out, double t, double dt, double *smax_out, void *stream);
 
+/* ---- three dimensions ---------------------------------------------------
+ * The paper implements two dimensions and states that the equations of its
+ * section 2 (eq. OurSystem) carry over directly to three (section 3 opening
+ * and the conclusions).  These entry points advance one 3D domain of the
+ * same balance laws with a third velocity component:
+ *     q = (rho/rho0)(1, u1/c0, u2/c0, u3/c0)          (eq. adim:q in 3D)
+ * by the fractional steps x1 sweep, x2 sweep, x3 sweep, source (eqs.
+ * fs:cl1-fs:source with a third directional step), each sweep eq. fv-hr with
+ * the Roe solver of section 3.2 extended by the fourth component (a second
+ * transverse family moving at u) and the MC-limited correction of eq.
+ * limiter; the source uses the 7-point Laplacian; dt follows section 4's CFL
+ * rule over all three directions.  States cross the boundary as four planes
+ * of nx*ny*nz binary64 total variables (q1, q2, q3, q4), field f, cell
+ * (i, j, k) at f*nx*ny*nz + (k*ny + j)*nx + i.  In FVNA_FP32_PERT precision
+ * the device copy holds (q1 - 1, q2, q3, q4) in binary32. */
+typedef struct fvna_domain3 {
+  int nx, ny, nz;       /* cells; >= 1 each (>= 3 across a periodic or reflective pair) */
+  int bc[6];            /* x1-low, x1-high, x2-low, x2-high, x3-low, x3-high: FVNA_BC_PERIODIC
+                           (in pairs), FVNA_BC_EXTRAP or FVNA_BC_REFLECT */
+  int substeps;         /* 0: the full step; otherwise the sub-steps to take, bit 0 x1 sweep,
+                           bit 1 x2 sweep, bit 2 x3 sweep, bit 3 source */
+  double t0;            /* initial time */
+  double dt0;           /* > 0: dt of the first step; 0: from a speed pass over q0 */
+} fvna_domain3;
+
+typedef struct fvna3_ctx fvna3_ctx;
+
+/* fvna3_init -- create a 3D context.
+ *   cfg   precision (FVNA_FP64 or FVNA_FP32_PERT), limiter, beta, delta, dx,
+ *         nu_w, nu_max, dt_fixed, steps_per_graph and compensated as in 2D;
+ *         geometry must be FVNA_CARTESIAN and splitting FVNA_SPLIT_GODUNOV;
+ *         sweeps is not read (dom->substeps selects sub-steps); tile_y is
+ *         the height of the x2/x3 sweeps' tiles (0: 64)
+ *   dom   the domain (borrowed, copied)
+ *   q0    4*nx*ny*nz binary64 total variables in the layout above (borrowed,
+ *         copied; device memory if q0_on_device)
+ *   stream cudaStream_t to enqueue on (borrowed; NULL = legacy default)
+ * The first dt comes from a speed-only pass over q0 unless dt_fixed or dt0
+ * is set.  Returns FVNA_OK, FVNA_ERR_ARG for bad sizes, enums or border
+ * rules, FVNA_ERR_OOM or FVNA_ERR_CUDA; *out is NULL on failure. */
+int fvna3_init(const fvna_config *cfg, const fvna_domain3 *dom, const double *q0, int q0_on_device,
+               void *stream, fvna3_ctx **out);
+/* fvna3_run -- advance until t_end (the last step shortened to end on it;
+ * t_end <= t: no time limit) or max_steps steps; blocks.  Returns FVNA_OK or
+ * the first device status (FVNA_ERR_NONREAL, _CFL, _NAN); stats may be NULL. */
+int fvna3_run(fvna3_ctx *ctx, double t_end, long long max_steps, fvna_stats *stats);
+/* fvna3_step_timed -- one step launched kernel by kernel with CUDA events
+ * between the launches on the context's stream; blocks.  ms receives the
+ * device time in milliseconds of ms[0] the x1 sweep, ms[1] the x2 sweep,
+ * ms[2] the x3 sweep, ms[3] the source, ms[4] the dt update. */
+int fvna3_step_timed(fvna3_ctx *ctx, float ms[5]);
+/* fvna3_fields -- copy FVNA_FIELD_Q (4*nx*ny*nz binary64), FVNA_FIELD_PRESSURE
+ * (nx*ny*nz binary64 q1 - 1) or FVNA_FIELD_STATS (one fvna_stats) into a
+ * caller buffer of `bytes` bytes (host or device per dst_on_device);
+ * synchronises the stream.  FVNA_ERR_ARG if bytes is too small. */
+int fvna3_fields(fvna3_ctx *ctx, int what, void *dst, size_t bytes, int dst_on_device);
+/* fvna3_launch_count -- kernels this context has enqueued so far. */
+long long fvna3_launch_count(const fvna3_ctx *ctx);
+/* fvna3_destroy -- free the context and its device memory (NULL is a no-op). */
+void fvna3_destroy(fvna3_ctx *ctx);
+
 /* ---- learned sub-grid correction (not in the paper) ----------------------
  * A small convolutional network applied to coarse runs: three 3x3
  * convolutions with zero padding, 3 -> 32 -> 32 -> 3 channels, ReLU after

@@ -7,6 +7,9 @@ the static CUDA runtime:
   fvna_api.cu   host runtime behind include/fvna.h
   fvna_noalloc.cu  the allocation-free binary64 step (fixed device scratch array)
   fvna_net.cu   the learned correction (BF16 tensor-core forward, FP32 backward)
+  fvna_3d64.cu  the 3D step in binary64 (-fmad=false) and its dt bookkeeping
+  fvna_3d32.cu  the 3D step in binary32 perturbation variables
+  fvna_api3d.cu host runtime of the 3D entry points
 """
 from __future__ import annotations
 
@@ -28,6 +31,9 @@ UNITS = {
     "fvna_api": [],
     "fvna_noalloc": ["-fmad=false"],
     "fvna_net": [],
+    "fvna_3d64": ["-fmad=false"],
+    "fvna_3d32": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
+    "fvna_api3d": [],
 }
 
 

@@ -101,7 +101,9 @@ int validate(const fvna_config *c, int n, const fvna_domain *d, const double *co
   if (!(c->dt_fixed > 0.0) && !(c->nu_w > 0.0)) return FVNA_ERR_ARG;
   if (!(c->nu_max > 0.0)) return FVNA_ERR_ARG;
   if (c->steps_per_graph < 0 || c->steps_per_graph > 4096) return FVNA_ERR_ARG;
-  if (c->tile_x != 0 && c->tile_x != 16 && c->tile_x != 32 && c->tile_x != 64) return FVNA_ERR_ARG;
+  if (c->tile_x != 0 && c->tile_x != 16 && c->tile_x != 32 && c->tile_x != 64 &&
+      !(c->tile_x == X32H_TILE && c->precision == FVNA_FP32_PERT))
+    return FVNA_ERR_ARG;
   if (c->tile_y != 0 && (c->tile_y < 8 || c->tile_y > 4096)) return FVNA_ERR_ARG;
   if (c->compensated != 0 && c->compensated != 1) return FVNA_ERR_ARG;
   if (c->splitting != FVNA_SPLIT_GODUNOV && c->splitting != FVNA_SPLIT_STRANG) return FVNA_ERR_ARG;
@@ -449,13 +451,17 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   // longer and the sweeps hand tiles out in list order)
   std::vector<Tile> tx, ty, txb, tyb;
   const int sw = x32_half(c->tile_x);
-  const int xstep = prec == FVNA_FP64 ? c->tile_x : 2 * sw;
+  // binary32 x1 sweep with the lanes along x1: segments of two rows x 60 cells
+  const bool xh = prec == FVNA_FP32_PERT && c->tile_x == X32H_TILE;
+  const int xstep = prec == FVNA_FP64 ? c->tile_x : xh ? X32H_TILE : 2 * sw;
+  const int xrows = xh ? 2 : XROWS;
   const int ystep = prec == FVNA_FP64 ? YCOLS : Y32_COLS;
   for (int d = 0; d < n; d++) {
     const int nx = doms[d].nx, ny = doms[d].ny;
-    for (int y = 0; y < ny; y += XROWS)
+    for (int y = 0; y < ny; y += xrows)
       for (int x = 0; x < nx; x += xstep) {
-        bool b = prec == FVNA_FP32_PERT && (x == 0 || x + 2 * sw + 2 > nx || y + XROWS > ny);
+        bool b = xh ? (x < 2 || x + X32H_TILE + 2 > nx || y + 2 > ny)
+                    : prec == FVNA_FP32_PERT && (x == 0 || x + 2 * sw + 2 > nx || y + XROWS > ny);
         (b ? txb : tx).push_back(Tile{d, x, y, 0});
       }
     for (int y = 0; y < ny; y += c->tile_y)
@@ -819,7 +825,7 @@ int fvna_autotune(const fvna_config *cfg, int n, const fvna_domain *doms, const 
   if (!best || trial_steps < 1) return FVNA_ERR_ARG;
   int v = validate(cfg, n, doms, q0);
   if (v != FVNA_OK) return v;
-  static const int TX[3] = {16, 32, 64};
+  static const int TX[4] = {X32H_TILE, 16, 32, 64};
   static const int TY[5] = {8, 16, 32, 64, 128};
   float best_ms = -1.0f;
   fvna_config winner = *cfg;
@@ -831,10 +837,11 @@ int fvna_autotune(const fvna_config *cfg, int n, const fvna_domain *doms, const 
     return cuda_err(ce);
   }
   int rc = FVNA_OK;
-  for (int a = 0; a < 3 && rc == FVNA_OK; a++)
+  const int ntx = cfg->precision == FVNA_FP32_PERT ? 4 : 3;
+  for (int a = 0; a < ntx && rc == FVNA_OK; a++)
     for (int b = 0; b < 5 && rc == FVNA_OK; b++) {
       fvna_config trial = *cfg;
-      trial.tile_x = TX[a];
+      trial.tile_x = TX[cfg->precision == FVNA_FP32_PERT ? a : a + 1];
       trial.tile_y = TY[b];
       trial.steps_per_graph = trial_steps;
       fvna_ctx *c = new (std::nothrow) fvna_ctx();

@@ -11,6 +11,7 @@
 
 #include "fvna_launch.h"
 #include "fvna_sweeps32.cuh"
+#include "fvna_xh.cuh"
 
 #define POLICY P32
 #define SUFFIX fp32
@@ -20,7 +21,9 @@
 
 namespace fvna {
 
-// tile_x 16 / 32 / 64 -> halves of 8 / 16 / 32 cells (swizzle span 32 / 64 / 128 B)
+// tile_x 16 / 32 / 64 -> halves of 8 / 16 / 32 cells (swizzle span 32 / 64 / 128 B) of the
+// tile sweep; tile_x 60 selects the sweep with the lanes along x1 (no tensor maps of its own:
+// the maps built for it are those of 32-cell halves, unused)
 int x32_half(int tile_x) { return tile_x == 16 ? 8 : tile_x == 32 ? 16 : 32; }
 
 namespace {
@@ -35,7 +38,18 @@ template <int SW> StepKernel px_l(int lim, bool comp) {
   if (lim == LIM_LW) return px_c<SW, LIM_LW>(comp);
   return px_c<SW, LIM_MC>(comp);
 }
+template <int LIM> StepKernel pxh_c(bool comp) {
+  return comp ? k_sweep_x32h<LIM, true> : k_sweep_x32h<LIM, false>;
+}
+StepKernel pxh(int lim, bool comp) {
+  if (lim == LIM_NONE) return pxh_c<LIM_NONE>(comp);
+  if (lim == LIM_LW) return pxh_c<LIM_LW>(comp);
+  return pxh_c<LIM_MC>(comp);
+}
+// shared memory of the x1 sweep kernel a tile width selects
+int smem_x32(int tile_x) { return tile_x == XH_TILE ? 0 : x32_smem_bytes(x32_half(tile_x)); }
 StepKernel px(int tile_x, int lim, bool comp) {
+  if (tile_x == XH_TILE) return pxh(lim, comp);
   int sw = x32_half(tile_x);
   if (sw == 8) return px_l<8>(lim, comp);
   if (sw == 16) return px_l<16>(lim, comp);
@@ -105,7 +119,7 @@ __global__ void k_budget32(DomDev D, double *dst) {
 cudaError_t prepare_kernels_fp32(int tile_x, int lim, int comp) {
   cudaError_t e = cudaFuncSetAttribute(px(tile_x, lim, comp != 0),
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       x32_smem_bytes(x32_half(tile_x)));
+                                       smem_x32(tile_x));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(py<false>(lim, comp != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
                            y32_smem_bytes());
@@ -117,7 +131,7 @@ cudaError_t prepare_kernels_fp32(int tile_x, int lim, int comp) {
 int occupancy_x_fp32(int tile_x, int lim, int comp) {
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, px(tile_x, lim, comp != 0), 32,
-                                                x32_smem_bytes(x32_half(tile_x)));
+                                                smem_x32(tile_x));
   return n;
 }
 int occupancy_y_fp32(int lim, int comp) {
@@ -128,7 +142,7 @@ int occupancy_y_fp32(int lim, int comp) {
 }
 
 cudaError_t launch_sweep_x_fp32(int tile_x, const StepArgs &a, int blocks, cudaStream_t s) {
-  px(tile_x, a.limiter, a.compensated != 0)<<<blocks, 32, x32_smem_bytes(x32_half(tile_x)), s>>>(a);
+  px(tile_x, a.limiter, a.compensated != 0)<<<blocks, 32, smem_x32(tile_x), s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_sweep_y_fp32(const StepArgs &a, int blocks, cudaStream_t s) {

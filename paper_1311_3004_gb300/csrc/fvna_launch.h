@@ -76,6 +76,8 @@ int occupancy_y_fp32(int lim, int comp);
 // (device array, cudaFree to release); budgets on demand (sum of the state,
 // binary64, into dst[3] on the device)
 int x32_half(int tile_x);
+// tile_x of the binary32 x1 sweep with the lanes along x1 (segments of two rows x 60 cells)
+constexpr int X32H_TILE = 60;
 constexpr int Y32_COLS = 60;
 cudaError_t build_maps_fp32(const DomDev *dd, int n, int tile_x, void **d_maps, cudaStream_t s);
 cudaError_t launch_budget_fp32(const DomDev &d, double *dst, cudaStream_t s);

@@ -59,6 +59,12 @@ class Domain(ctypes.Structure):
                 ("aperture", ctypes.c_double)]
 
 
+class Domain3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("bc", ctypes.c_int * 6), ("substeps", ctypes.c_int),
+                ("t0", ctypes.c_double), ("dt0", ctypes.c_double)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("t", ctypes.c_double), ("dt", ctypes.c_double),
                 ("dt_last", ctypes.c_double), ("smax", ctypes.c_double),
@@ -75,7 +81,8 @@ SYMBOLS = ["fvna_init", "fvna_step", "fvna_run", "fvna_sync", "fvna_fields",
            "fvna_last_cuda_error",
            "fvna_step_noalloc", "fvna_autotune", "fvna_net_create", "fvna_net_params",
            "fvna_net_forward", "fvna_net_backward", "fvna_net_train_step", "fvna_net_destroy",
-           "fvna_set_correction"]
+           "fvna_set_correction", "fvna3_init", "fvna3_run", "fvna3_step_timed", "fvna3_fields",
+           "fvna3_launch_count", "fvna3_destroy"]
 
 _lib = None
 
@@ -146,6 +153,19 @@ def lib():
     L.fvna_step_noalloc.restype = ctypes.c_int
     L.fvna_step_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Domain), vp, vp,
                                     ctypes.c_double, ctypes.c_double, dp, vp]
+    L.fvna3_init.restype = ctypes.c_int
+    L.fvna3_init.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Domain3), vp, ctypes.c_int, vp,
+                             ctypes.POINTER(vp)]
+    L.fvna3_run.restype = ctypes.c_int
+    L.fvna3_run.argtypes = [vp, ctypes.c_double, ctypes.c_longlong, ctypes.POINTER(Stats)]
+    L.fvna3_step_timed.restype = ctypes.c_int
+    L.fvna3_step_timed.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    L.fvna3_fields.restype = ctypes.c_int
+    L.fvna3_fields.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t, ctypes.c_int]
+    L.fvna3_launch_count.restype = ctypes.c_longlong
+    L.fvna3_launch_count.argtypes = [vp]
+    L.fvna3_destroy.restype = None
+    L.fvna3_destroy.argtypes = [vp]
     L.fvna_riemann.restype = ctypes.c_int
     L.fvna_riemann.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, dp, dp, dp, dp]
     _lib = L
@@ -223,6 +243,88 @@ def autotune(config: Config, domains: Sequence[Domain], q0: Sequence, trial_step
                                ctypes.c_void_p(stream), int(trial_steps), ctypes.byref(best),
                                ctypes.byref(ms)), "fvna_autotune")
     return best, float(ms.value)
+
+
+def make_domain3(nx, ny, nz, bc=(BC_EXTRAP,) * 6, t0=0.0, dt0=0.0, substeps=0) -> Domain3:
+    """substeps: 0 the full step, else bit 0 x1, bit 1 x2, bit 2 x3, bit 3 source."""
+    return Domain3(nx, ny, nz, (ctypes.c_int * 6)(*bc), substeps, t0, dt0)
+
+
+class Solver3:
+    """One 3D domain (fvna3_*).  q0: (4, nz, ny, nx) binary64 total variables,
+    a numpy array (host) or a torch CUDA tensor (device).  domain.substeps
+    selects sub-steps (0: the full step)."""
+
+    def __init__(self, config: Config, domain: Domain3, q0, stream=None):
+        L = lib()
+        self.config = config
+        self.domain = domain
+        shape = (4, domain.nz, domain.ny, domain.nx)
+        if hasattr(q0, "is_cuda") and q0.is_cuda:
+            import torch
+            q = q0.to(torch.float64).contiguous()
+            on_dev, ptr = 1, q.data_ptr()
+        else:
+            q = np.ascontiguousarray(q0, dtype=np.float64)
+            on_dev, ptr = 0, q.ctypes.data
+        assert tuple(q.shape) == shape, (tuple(q.shape), shape)
+        if stream is None:
+            stream = _current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(L.fvna3_init(ctypes.byref(config), ctypes.byref(domain), ctypes.c_void_p(ptr),
+                            on_dev, ctypes.c_void_p(stream), ctypes.byref(h)), "fvna3_init")
+        self._h = h
+
+    def run(self, t_end: float = -np.inf, max_steps: int = 2 ** 62, check: bool = True) -> dict:
+        st = Stats()
+        t_end = float(t_end) if np.isfinite(t_end) else -1e300
+        rc = lib().fvna3_run(self._h, t_end, int(max_steps), ctypes.byref(st))
+        if check:
+            _check(rc, "fvna3_run")
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
+
+    def step_timed(self):
+        """One step with per-kernel device times (ms): x1, x2, x3 sweeps, source, dt update."""
+        ms = (ctypes.c_float * 5)()
+        _check(lib().fvna3_step_timed(self._h, ms), "fvna3_step_timed")
+        return tuple(float(x) for x in ms)
+
+    def q(self, out=None):
+        """State as (4, nz, ny, nx) binary64 (numpy, or into a torch CUDA tensor)."""
+        d = self.domain
+        n = 4 * d.nx * d.ny * d.nz
+        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            _check(lib().fvna3_fields(self._h, FIELD_Q, ctypes.c_void_p(out.data_ptr()),
+                                      out.numel() * out.element_size(), 1), "fvna3_fields")
+            return out
+        q = np.empty((4, d.nz, d.ny, d.nx), dtype=np.float64)
+        _check(lib().fvna3_fields(self._h, FIELD_Q, q.ctypes.data_as(ctypes.c_void_p), n * 8, 0),
+               "fvna3_fields")
+        return q
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(lib().fvna3_fields(self._h, FIELD_STATS, ctypes.cast(ctypes.byref(st),
+                                                                    ctypes.c_void_p),
+                                  ctypes.sizeof(st), 0), "fvna3_fields")
+        return st.as_dict()
+
+    def launch_count(self) -> int:
+        return int(lib().fvna3_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fvna3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:

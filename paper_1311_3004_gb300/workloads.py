@@ -237,3 +237,55 @@ def hifu_cartesian(eta: float, aperture: float, window=None, focal: float = 50.0
                     0.9, (BC_HIFU, BC_EXTRAP, BC_REFLECT, BC_EXTRAP), ambient(nx, ny),
                     extra={"amp": amp, "focal": focal, "aperture": aperture, "envelope": 1,
                            "t0": t0, "t1": 6.0})
+
+
+# ---------------------------------------------------------------- three dimensions
+
+def ambient3(nx: int, ny: int, nz: int) -> np.ndarray:
+    """State at rest in 3D: (4, nz, ny, nx) with q1 = 1."""
+    q = np.zeros((4, nz, ny, nx))
+    q[0] = 1.0
+    return q
+
+
+def gaussian_pulse3(nx: int, ny: int, nz: int, amp: float, sigma_cells: float, seed: int,
+                    max_offset: float = 0.125) -> np.ndarray:
+    """3D Gaussian pressure pulse at rest: q1 = 1 + amp exp(-r^2 / (2 sigma^2)),
+    the centre offset from the box centre by a seeded fraction (up to
+    max_offset of each side)."""
+    rng = np.random.default_rng(seed)
+    off = rng.uniform(-max_offset, max_offset, size=3)
+    c = [(n / 2.0) * (1.0 + 2.0 * o) for n, o in zip((nx, ny, nz), off)]
+    z = (np.arange(nz) + 0.5 - c[2])[:, None, None]
+    y = (np.arange(ny) + 0.5 - c[1])[None, :, None]
+    x = (np.arange(nx) + 0.5 - c[0])[None, None, :]
+    q = ambient3(nx, ny, nz)
+    q[0] += amp * np.exp(-(x * x + y * y + z * z) / (2.0 * sigma_cells ** 2))
+    return q
+
+
+def random_smooth3(nx: int, ny: int, nz: int, amp: float, seed: int, modes: int = 4) -> np.ndarray:
+    """Sum of a few random Fourier modes in all four fields (periodic-friendly)."""
+    rng = np.random.default_rng(seed)
+    z = (np.arange(nz) / nz)[:, None, None]
+    y = (np.arange(ny) / ny)[None, :, None]
+    x = (np.arange(nx) / nx)[None, None, :]
+    q = ambient3(nx, ny, nz)
+    for f in range(4):
+        acc = np.zeros((nz, ny, nx))
+        for _ in range(modes):
+            kx, ky, kz = rng.integers(0, 4, size=3)
+            ph = rng.uniform(0, 2 * np.pi)
+            acc += rng.uniform(-1, 1) * np.cos(2 * np.pi * (kx * x + ky * y + kz * z) + ph)
+        q[f] += amp * acc / modes
+    return q
+
+
+def gaussian3d(n: int = 256, seed: int = 2) -> dict:
+    """The 2D pulse workload's 3D counterpart: an n^3 box (256^3 by default),
+    peak 2 MPa, sigma 8 cells, centre offset from the seed, extrapolation on
+    all six faces, water at 1 MHz with 40 cells per wavelength."""
+    return {"name": f"gaussian3d_{n}", "n": n, "q0": gaussian_pulse3(n, n, n, amplitude(2.0e6), 8.0,
+                                                                      seed),
+            "beta": beta_of(), "delta": delta_tilde(1.0e6), "dx": 1.0 / 40, "nu_w": 0.9,
+            "bc": (BC_EXTRAP,) * 6}

@@ -46,12 +46,15 @@ def test_struct_layout_matches_header():
 #include "fvna.h"
 #define P(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
 int main(void) {
-  printf("fvna_config %zu\nfvna_domain %zu\nfvna_stats %zu\n", sizeof(fvna_config),
-         sizeof(fvna_domain), sizeof(fvna_stats));
+  printf("fvna_config %zu\nfvna_domain %zu\nfvna_stats %zu\nfvna_domain3 %zu\n",
+         sizeof(fvna_config), sizeof(fvna_domain), sizeof(fvna_stats), sizeof(fvna_domain3));
   P(fvna_config, beta); P(fvna_config, dt_fixed); P(fvna_config, tile_y);
   P(fvna_config, compensated); P(fvna_config, splitting);
   P(fvna_domain, x0); P(fvna_domain, dt0); P(fvna_domain, aperture);
   P(fvna_stats, nu_std); P(fvna_stats, status);
+  P(fvna_config, wait_limit);
+  P(fvna_domain3, nz); P(fvna_domain3, bc); P(fvna_domain3, substeps); P(fvna_domain3, t0);
+  P(fvna_domain3, dt0);
   return 0;
 }
 """
@@ -65,11 +68,12 @@ int main(void) {
     assert int(got["fvna_config"]) == ctypes.sizeof(fvna.Config)
     assert int(got["fvna_domain"]) == ctypes.sizeof(fvna.Domain)
     assert int(got["fvna_stats"]) == ctypes.sizeof(fvna.Stats)
+    assert int(got["fvna_domain3"]) == ctypes.sizeof(fvna.Domain3)
     for key, v in got.items():
         if "." in key:
             T, f = key.split(".")
             cls = {"fvna_config": fvna.Config, "fvna_domain": fvna.Domain,
-                   "fvna_stats": fvna.Stats}[T]
+                   "fvna_stats": fvna.Stats, "fvna_domain3": fvna.Domain3}[T]
             assert getattr(cls, f).offset == int(v), key
 
 

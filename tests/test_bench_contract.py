@@ -39,9 +39,10 @@ def test_traffic_record_is_keyed_to_the_sources(tmp_path):
     def row(i, name, metric, v):
         return (f'"{i}","1","python","h","{name}","1","7","(32, 1, 1)","(9, 1, 1)","0","10.3",'
                 f'"Command line profiler metrics","{metric}","byte","{v}"')
-    x = "void fvna::k_sweep_x32<32, 0, true>(fvna::StepArgs)"
-    y1 = "void fvna::k_sweep_y32<0, true, false>(fvna::StepArgs)"
-    y2 = "void fvna::k_sweep_y32<0, true, true>(fvna::StepArgs)"
+    # the names as ncu prints them: no namespaces, bools as 0 / 1
+    x = "void k_sweep_x32<32, 0, 1>(StepArgs)"
+    y1 = "void k_sweep_y32<0, 1, 0>(StepArgs)"
+    y2 = "void k_sweep_y32<0, 1, 1>(StepArgs)"
     lines = ["==PROF== Connected", hdr]
     for s in range(2):
         b = 10 * s

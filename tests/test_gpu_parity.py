@@ -110,6 +110,15 @@ TOL32 = 1e-5   # binary32 perturbation form against the binary64 oracle (perturb
 
 
 @pytest.mark.parametrize("name,case,steps", _cases(), ids=[c[0] for c in _cases()])
+def test_step_parity_fp32_lanes_along_x1(name, case, steps):
+    """Every parity case with the x1 sweep that puts the lanes along x1."""
+    qo, so = run_oracle(case, steps)
+    qg, sg = run_gpu(case, steps, precision=fvna.FP32_PERT, tile_x=60)
+    assert sg["rc"] == 0 and so["status"] == 0
+    assert pert_rel_linf(qg, qo) <= TOL32
+
+
+@pytest.mark.parametrize("name,case,steps", _cases(), ids=[c[0] for c in _cases()])
 def test_step_parity_fp32(name, case, steps):
     """Every case above through the binary32 kernels (borders, limiters,
     sweeps switched off, one-row and one-column domains, fixed dt)."""
@@ -124,11 +133,12 @@ def test_step_parity_fp32(name, case, steps):
 
 @pytest.mark.parametrize("tile_x,tile_y,compensated",
                          [(16, 10, 1), (32, 18, 1), (64, 18, 1), (16, 8, 0), (32, 64, 0),
-                          (64, 34, 1), (64, 8, 0)])
+                          (64, 34, 1), (64, 8, 0), (60, 18, 1), (60, 8, 0), (60, 42, 1)])
 def test_fp32_tile_shapes(tile_x, tile_y, compensated):
     """The binary32 sweeps for every x1 tile width (halves of 8, 16, 32 cells:
-    the three TMA swizzle spans), several x2 tile heights (ring chunks full
-    and ragged) and both update forms, against the oracle."""
+    the three TMA swizzle spans; 60: the x1 sweep with the lanes along x1),
+    several x2 tile heights (ring chunks full and ragged) and both update
+    forms, against the oracle."""
     q = wl.random_cells(150, 140, 1e-3, seed=31)
     c = Case(150, 140, q, bc=(P, P, E, R), delta=2e-3)
     qo, _ = run_oracle(c, 15)
@@ -329,20 +339,22 @@ def test_fp32_perturbation_against_fp64_oracle():
     assert abs(sg["t"] - so["t"]) <= 1e-6 * so["t"]
 
 
-@pytest.mark.parametrize("bc", [(P, P, P, P), (R, E, T, E)])
-def test_fp32_borders_against_fp64(bc):
+@pytest.mark.parametrize("tile_x", [0, 60])
+@pytest.mark.parametrize("bc", [(P, P, P, P), (R, E, T, E), (T, T, R, E)])
+def test_fp32_borders_against_fp64(bc, tile_x):
     n = 96
     q = wl.random_smooth(n, n, 1e-3, seed=57)
     c = Case(n, n, q, bc=bc, beta=3.5, delta=2e-3, dx=1.0 / 24, taylor_ratio=1e-4, y0=0.0)
     qo, _ = run_oracle(c, 100)
-    qg, sg = run_gpu(c, 100, precision=fvna.FP32_PERT)
+    qg, sg = run_gpu(c, 100, precision=fvna.FP32_PERT, tile_x=tile_x)
     assert sg["rc"] == 0
     peak, l2 = pressure_errors(qg[0] - 1.0, qo[0] - 1.0)
     assert peak <= 1e-5 and l2 <= 1e-5, (peak, l2)
 
 
+@pytest.mark.parametrize("tile_x", [0, 60])
 @pytest.mark.parametrize("flow", [(0.75, 0.0), (0.0, 0.75)])
-def test_fp32_faces_that_are_not_subsonic(flow):
+def test_fp32_faces_that_are_not_subsonic(flow, tile_x):
     """A uniform flow along x1 or x2 fast enough that the second family
     moves the same way as the first (this system has c^2 = 1 - u^2 + ...,
     so that is 1/sqrt(2) < |u| < 1), with a small perturbation on top: the
@@ -357,7 +369,7 @@ def test_fp32_faces_that_are_not_subsonic(flow):
     c = Case(n, n, q, bc=(P, P, P, P), beta=3.5, delta=1e-3, dx=1.0 / 32)
     qo, so = run_oracle(c, 60)
     assert so["status"] == 0 and so["smax"] > 1.3
-    qg, sg = run_gpu(c, 60, precision=fvna.FP32_PERT)
+    qg, sg = run_gpu(c, 60, precision=fvna.FP32_PERT, tile_x=tile_x)
     assert sg["rc"] == 0 and sg["steps"] == so["step"]
     assert pert_rel_linf(qg, qo) <= 1e-5
     q64, _ = run_gpu(c, 60)
@@ -453,7 +465,7 @@ def test_batched_domains_fp32_and_autotune():
     cfg = gpu_config(cases[0], fvna.FP32_PERT)
     doms = [gpu_domain(c) for c in cases]
     best, ms = fvna.autotune(cfg, doms, [c.q0 for c in cases], trial_steps=4)
-    assert best.tile_x in (16, 32, 64) and best.tile_y in (8, 16, 32, 64, 128) and ms > 0
+    assert best.tile_x in (60, 16, 32, 64) and best.tile_y in (8, 16, 32, 64, 128) and ms > 0
     s = fvna.Solver(best, doms, [c.q0 for c in cases])
     s.run(max_steps=60)
     for k, c in enumerate(cases):
