@@ -65,8 +65,12 @@ def parse():
                     help="side of the square window of the rotated Taylor shocks (units of x)")
     ap.add_argument("--taylor-angles", default="0,32,16,8,4",
                     help="theta_T = pi/k for these k (0: theta_T = 0)")
-    ap.add_argument("--taylor-etas", default="5,10,20,41,82")
+    ap.add_argument("--taylor-etas", default="5,10,20,41,82",
+                    help="eta of the rotated shocks")
+    ap.add_argument("--taylor-etas0", default="5,10,20,41,82", help="eta of theta_T = 0")
     ap.add_argument("--taylor-nus", default="0.6,0.7,0.8,0.9,0.99")
+    ap.add_argument("--hifu-nus", default="0.6,0.7,0.8,0.9,0.99")
+    ap.add_argument("--hifu-apertures", default="10,20,30")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile-x", type=int, default=0,
                     help="x1-sweep tile width (16/32/64; 0: the library's choice)")
@@ -76,8 +80,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--splitting", choices=["godunov", "strang"], default="godunov",
                     help="order of the fractional steps (the paper's: godunov)")
-    ap.add_argument("--plain-update", action="store_true",
-                    help="FP32 cell update as written instead of the compensated sum")
+    ap.add_argument("--compensated", action="store_true",
+                    help="FP32 cell update summed with error-free two-sums (default: one fused "
+                         "multiply-add of the summed increments, the more accurate form here)")
     ap.add_argument("--flush-mb", type=int, default=512,
                     help="L2 flush buffer written before every timed step (0: none)")
     ap.add_argument("--record-traffic", metavar="CSV",
@@ -310,7 +315,7 @@ def peaks():
 
 
 def measure_precision(torch, fvna, w, precision, steps, warmup, flush, do_flush=True,
-                      compensated=1, tiles=(0, 0), splitting=0):
+                      compensated=0, tiles=(0, 0), splitting=0):
     stream = torch.cuda.current_stream()
     cfg = fvna.make_config(precision=precision, beta=w.beta, delta=w.delta, dx=w.dx,
                            nu_w=w.nu_w, steps_per_graph=1, compensated=compensated,
@@ -359,7 +364,7 @@ def run_native(args):
     with ClockSampler(dev_index) as clk:
         per, launches, st = measure_precision(torch, fvna, w, prec, args.steps, args.warmup,
                                               flush, args.flush_mb > 0,
-                                              0 if args.plain_update else 1,
+                                              1 if args.compensated else 0,
                                               (args.tile_x, args.tile_y),
                                               1 if args.splitting == "strang" else 0)
     torch.cuda.synchronize()
@@ -394,7 +399,7 @@ def run_native(args):
         "data": "synthetic",
         "config": {"workload": f"gaussian_pulse_{w.nx}x{w.ny}", "cells_per_gpu": cells,
                    "precision": args.precision, "time_steps_per_bench_step": 1,
-                   "compensated_update": (not args.plain_update) and args.precision == "fp32",
+                   "compensated_update": bool(args.compensated) and args.precision == "fp32",
                    "splitting": args.splitting,
                    "l2": (f"flushed before every timed step ({args.flush_mb} MB write)"
                           if args.flush_mb > 0 else "not flushed"),
@@ -406,7 +411,7 @@ def run_native(args):
     }
 
     if not args.no_e2e:
-        line["e2e"] = e2e(torch, fvna, w, prec, 0 if args.plain_update else 1,
+        line["e2e"] = e2e(torch, fvna, w, prec, 1 if args.compensated else 0,
                           splitting=1 if args.splitting == "strang" else 0)
     if prec == fvna.FP32_PERT and not args.no_fp64:
         per64, _, _ = measure_precision(torch, fvna, w, fvna.FP64, max(3, args.steps // 10), 2,
@@ -424,7 +429,7 @@ def run_native(args):
     return 0
 
 
-def e2e(torch, fvna, w, prec, compensated=1, reps=2, splitting=0):
+def e2e(torch, fvna, w, prec, compensated=0, reps=2, splitting=0):
     """Whole-run call sequence from pinned host memory, host wall clock."""
     cells = w.nx * w.ny
     q_host = torch.from_numpy(w.q0).pin_memory()
@@ -538,12 +543,14 @@ def run_taylor(args):
     torch, fvna = _setup_cuda()
     from paper_1311_3004_gb300 import analysis
     ratio, beta, T = 1e-7, 3.5, 100.0
-    etas = [int(e) for e in args.taylor_etas.split(",")]
+    etas_rot = [int(e) for e in args.taylor_etas.split(",")]
+    etas_0 = [int(e) for e in args.taylor_etas0.split(",")]
     nus = [float(v) for v in args.taylor_nus.split(",")]
     ext = float(args.taylor_extent)
     table, cell_updates, total_s, runs = {}, 0.0, 0.0, []
     for k in (int(a) for a in args.taylor_angles.split(",")):
         angle = 0.0 if k == 0 else np.pi / k
+        etas = etas_0 if k == 0 else etas_rot
         rows = {"E1": [], "Einf": []}
         for nu in nus:
             e1s, eis = [], []
@@ -584,11 +591,14 @@ def run_taylor(args):
         table[key] = {n: {"rate_best": max(r[0] for r in v), "rate_worst": min(r[0] for r in v),
                           "rate_mean": float(np.mean([r[0] for r in v])),
                           "worst_r2": min(r[1] for r in v),
-                          "err82_best": min(r[2] for r in v), "err82_worst": max(r[2] for r in v)}
+                          "finest_eta": etas[-1],
+                          "err_finest_best": min(r[2] for r in v),
+                          "err_finest_worst": max(r[2] for r in v)}
                       for n, v in rows.items()}
     print(json.dumps({"metric": METRIC, "value": cell_updates / total_s, "unit": METRIC,
                       "workload": "taylor_shock_study_moving_window", "dtype": "f64",
-                      "window_extent": ext, "etas": etas, "nus": nus,
+                      "window_extent": ext, "etas_rotated": etas_rot, "etas_0": etas_0,
+                      "nus": nus,
                       "cell_updates": cell_updates, "time_s": total_s, "table": table,
                       "runs": runs}),
           flush=True)
@@ -597,79 +607,114 @@ def run_taylor(args):
 
 def run_hifu(args):
     """The focused packet of section 4.2 (F = 50, a = 10, 20, 30, beta = 4.8,
-    A = 4.217e-4, dt~ = 2.974e-4, nu_W = 0.9) in its two stages on a window
-    of 28 x (a + 10) wavelengths that follows the packet, binary64, eta = 20,
-    41, 82 cells per wavelength, to t = 100.  Per aperture: the on-axis
-    pressure maxima (peak value and position), their self-convergence (E_1,
-    E_inf of eta = 20 and 41 against eta = 82, evaluated as in section 4.1 on
-    the eta = 82 maxima interpolated to the coarser lab cells, x1 in [5,
-    95]), the harmonics at the focus (x1 = F, on the axis), the time to
-    solution; and the binary32 run at eta = 82 against the binary64 one."""
+    A = 4.217e-4, dt~ = 2.974e-4) in its two stages on a window of 28 x (a +
+    10) wavelengths that follows the packet, binary64, eta = 20, 41, 82 cells
+    per wavelength, to t = 100, for each nu_W of --hifu-nus.  Per aperture and
+    nu_W: the on-axis pressure maxima of the packet's central peak (the
+    paper's measure; the maxima over the whole passage beside them), their
+    self-convergence (E_1, E_inf of eta = 20 and 41 against eta = 82 at the
+    same nu_W, on the eta = 82 maxima interpolated to the coarser lab cells,
+    x1 in [5, 95]) and its order; the best, worst and mean over nu_W as the
+    paper's Table tab:error-hifu lists them; the harmonics at the focus; the
+    time to solution; and the binary32 run at eta = 82, nu_W = 0.9 against
+    the binary64 one."""
     torch, fvna = _setup_cuda()
     from paper_1311_3004_gb300 import analysis
     t_end, etas = 100.0, [20, 41, 82]
+    nus = [float(v) for v in args.hifu_nus.split(",")]
+    apertures = [float(v) for v in args.hifu_apertures.split(",")]
     amp = wl.hifu_cartesian(5.0, 10.0, window=(1.0, 1.0)).extra["amp"]
     out, cell_updates, total_s = {}, 0.0, 0.0
 
-    def one(eta, a, prec):
+    def one(eta, a, prec, nu):
         w = wl.hifu_cartesian(eta, a)
         e = w.extra
-        cfg = fvna.make_config(precision=prec, beta=w.beta, delta=w.delta, dx=w.dx, nu_w=w.nu_w,
+        cfg = fvna.make_config(precision=prec, beta=w.beta, delta=w.delta, dx=w.dx, nu_w=nu,
                                steps_per_graph=1)
         dom = fvna.make_domain(w.nx, w.ny, bc=w.bc, envelope=e["envelope"], t0=e["t0"],
                                amp=e["amp"], focal=e["focal"], aperture=e["aperture"])
         s = fvna.Solver(cfg, [dom], [w.q0])
         lab_cells = int((t_end - e["t1"] + w.nx * w.dx + 2) / w.dx)
-        (lab, tt, pp), sec = _timed(torch, lambda: analysis.focused_axis_run(
-            s, w.dx, e["t1"], t_end, e["focal"], lab_cells, from_bc=fvna.BC_EXTRAP))
+        (lab, tt, pp, cen), sec = _timed(torch, lambda: analysis.focused_axis_run(
+            s, w.dx, e["t1"], t_end, e["focal"], lab_cells, from_bc=fvna.BC_EXTRAP,
+            central=True))
         steps = s.stats(0)["steps"]
         s.close()
         x = (np.arange(lab_cells) + 0.5) * w.dx
-        return x, lab, tt, pp, sec, steps * w.nx * w.ny
+        return x, lab, cen, tt, pp, sec, steps * w.nx * w.ny
 
-    for a in (10.0, 20.0, 30.0):
-        res = {}
-        for eta in etas:
-            x, lab, tt, pp, sec, cu = one(eta, a, fvna.FP64)
-            res[eta] = (x, lab, tt, pp, sec)
-            cell_updates += cu
-            total_s += sec
-        xr, lr = res[82][0], res[82][1]
-        conv = {}
-        for eta in (20, 41):
-            x, lab = res[eta][0], res[eta][1]
-            sel = (x >= 5.0) & (x <= 95.0)
-            ref = np.interp(x[sel], xr, lr)
-            conv[str(eta)] = {"E1": float(np.sum(np.abs(lab[sel] - ref)) / np.sum(np.abs(ref))),
-                              "Einf": float(np.max(np.abs(lab[sel] - ref)) / np.max(np.abs(ref)))}
-        line = {}
-        for eta in etas:
-            x, lab, tt, pp, sec = res[eta]
-            sel = (x >= 5.0) & (x <= 95.0)
-            k = int(np.argmax(np.where(sel, lab, -np.inf)))
-            line[str(eta)] = {"peak": float(lab[k]), "peak_x1": float(x[k]),
-                              "gain": float(lab[k] / amp),
-                              "time_s": sec,
-                              "harmonics_at_focus": analysis.harmonics(tt, pp) if len(tt) > 8
-                              else None}
-        rate = {n: float(np.log(conv["20"][n] / conv["41"][n]) / np.log(41.0 / 20.0))
-                for n in ("E1", "Einf")}
-        x32, l32, _, _, sec32, _ = one(82, a, fvna.FP32_PERT)
-        sel = (x32 >= 5.0) & (x32 <= 95.0)
-        fp32 = {"time_s": sec32,
-                "axis_max_rel_err": float(np.max(np.abs(l32[sel] - lr[sel])) / np.max(lr[sel]))}
-        out[f"a={a:g}"] = {"eta": line, "self_convergence_vs_eta82": conv,
-                           "rate_20_41": rate, "fp32_eta82": fp32}
+    def errors(x, v, xr, vr):
+        sel = (x >= 5.0) & (x <= 95.0)
+        ref = np.interp(x[sel], xr, vr)
+        return {"E1": float(np.sum(np.abs(v[sel] - ref)) / np.sum(np.abs(ref))),
+                "Einf": float(np.max(np.abs(v[sel] - ref)) / np.max(np.abs(ref)))}
+
+    for a in apertures:
+        per_nu = {}
+        for nu in nus:
+            res = {}
+            for eta in etas:
+                x, lab, cen, tt, pp, sec, cu = one(eta, a, fvna.FP64, nu)
+                res[eta] = (x, lab, cen, tt, pp, sec)
+                cell_updates += cu
+                total_s += sec
+            xr = res[82][0]
+            conv = {"central": {}, "passage": {}}
+            for eta in (20, 41):
+                conv["central"][str(eta)] = errors(res[eta][0], res[eta][2], xr, res[82][2])
+                conv["passage"][str(eta)] = errors(res[eta][0], res[eta][1], xr, res[82][1])
+            line = {}
+            for eta in etas:
+                x, lab, cen, tt, pp, sec = res[eta]
+                sel = (x >= 5.0) & (x <= 95.0)
+                k = int(np.argmax(np.where(sel, cen, -np.inf)))
+                kp = int(np.argmax(np.where(sel, lab, -np.inf)))
+                line[str(eta)] = {"peak": float(cen[k]), "peak_x1": float(x[k]),
+                                  "gain": float(cen[k] / amp),
+                                  "passage_peak": float(lab[kp]), "passage_peak_x1": float(x[kp]),
+                                  "time_s": sec,
+                                  "harmonics_at_focus": analysis.harmonics(tt, pp)
+                                  if len(tt) > 8 and nu == 0.9 else None}
+            rate = {m: {n: float(np.log(conv[m]["20"][n] / conv[m]["41"][n]) / np.log(41.0 / 20.0))
+                        for n in ("E1", "Einf")} for m in conv}
+            per_nu[f"{nu:g}"] = {"eta": line, "self_convergence_vs_eta82": conv,
+                                 "rate_20_41": rate, "central82": res[82][2], "x82": xr}
+        # the paper's table form over nu_W (central-peak maxima)
+        table = {}
+        for n in ("E1", "Einf"):
+            rates = [per_nu[k]["rate_20_41"]["central"][n] for k in per_nu]
+            e41 = [per_nu[k]["self_convergence_vs_eta82"]["central"]["41"][n] for k in per_nu]
+            table[n] = {"rate_best": max(rates), "rate_worst": min(rates),
+                        "rate_mean": float(np.mean(rates)), "err41_best": min(e41),
+                        "err41_worst": max(e41)}
+        ref_nu = f"{max(nus):g}"
+        spread = {k: errors(per_nu[k]["x82"], per_nu[k]["central82"], per_nu[ref_nu]["x82"],
+                            per_nu[ref_nu]["central82"]) for k in per_nu if k != ref_nu}
+        res32 = None
+        if 0.9 in nus:
+            x32, l32, c32, _, _, sec32, _ = one(82, a, fvna.FP32_PERT, 0.9)
+            sel = (x32 >= 5.0) & (x32 <= 95.0)
+            r64 = per_nu["0.9"]["central82"]
+            res32 = {"time_s": sec32,
+                     "axis_max_rel_err": float(np.max(np.abs(c32[sel] - r64[sel])) /
+                                               np.max(r64[sel]))}
+        for k in per_nu:
+            per_nu[k].pop("central82")
+            per_nu[k].pop("x82")
+        out[f"a={a:g}"] = {"per_nu_w": per_nu, "table_over_nu_w": table,
+                           f"eta82_vs_nu_w_{ref_nu}": spread, "fp32_eta82_nu0.9": res32}
     print(json.dumps({"metric": METRIC, "value": cell_updates / total_s, "unit": METRIC,
                       "workload": "focused_packet_two_stage_moving_window", "dtype": "f64",
-                      "cell_updates": cell_updates, "time_s": total_s, "results": out}),
-          flush=True)
+                      "nus": nus, "cell_updates": cell_updates, "time_s": total_s,
+                      "results": out}), flush=True)
     return 0
 
 
 def run_batched(args):
     """64 domains of uneven size in one context (one launch per sub-step over
     all of them), FP32, autotuned tiles, 1000 steps each with its own dt;
+    against the same FP32 kernels run domain by domain (a context per domain,
+    one after the other, each with its own graph: what batching buys), and
     against the plain FP64 solver looping over the domains one at a time
     (timed over the first `fp64_steps` steps and scaled to 1000)."""
     torch, fvna = _setup_cuda()
@@ -690,6 +735,20 @@ def run_batched(args):
     _, sec32 = _timed(torch, lambda: s.run(max_steps=steps))
     launches = s.launch_count() - n0
     s.close()
+    # the same binary32 step, one domain at a time (library-default tiles)
+    cfg32 = fvna.make_config(precision=fvna.FP32_PERT, beta=beta, delta=delta, dx=dx, nu_w=0.9,
+                             steps_per_graph=50)
+
+    ctxs = [fvna.Solver(cfg32, [d], [qd[k]]) for k, d in enumerate(doms)]
+    for c1 in ctxs:                     # capture every context's graph first
+        c1.run(max_steps=1)
+
+    def one_by_one():
+        for c1 in ctxs:
+            c1.run(max_steps=steps)
+    _, sec32_seq = _timed(torch, one_by_one)
+    for c1 in ctxs:
+        c1.close()
     # plain FP64, one domain at a time, first fp64_steps steps
     cfg64 = fvna.make_config(precision=fvna.FP64, beta=beta, delta=delta, dx=dx, nu_w=0.9,
                              steps_per_graph=50)
@@ -722,6 +781,11 @@ def run_batched(args):
                                       "time_to_solution_s_scaled": sec64 * steps / fp64_steps,
                                       "measured_steps": fp64_steps},
             "speedup_vs_plain_fp64": (sec64 * steps / fp64_steps) / sec32,
+            "fp32_one_domain_at_a_time": {"time_to_solution_s": sec32_seq,
+                                          "value": cells * steps / sec32_seq,
+                                          "note": "a context per domain (created and its "
+                                                  "graph captured beforehand), run in turn"},
+            "speedup_vs_fp32_one_by_one": sec32_seq / sec32,
             "peak_rel_err_vs_fp64_max": max(errs), "peak_err_domains": len(errs)}
     print(json.dumps(line), flush=True)
     return 0
@@ -748,7 +812,7 @@ def run_gaussian3d(args):
                                   (fvna.FP64, "fp64", max(3, args.steps // 10))):
             cfg = fvna.make_config(precision=prec, beta=w["beta"], delta=w["delta"], dx=w["dx"],
                                    nu_w=w["nu_w"],
-                                   compensated=0 if args.plain_update else 1)
+                                   compensated=1 if args.compensated else 0)
             s = fvna.Solver3(cfg, fvna.make_domain3(n, n, n, w["bc"]), w["q0"])
             for _ in range(args.warmup):
                 if args.flush_mb > 0:

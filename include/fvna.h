@@ -78,8 +78,10 @@ enum fvna_field {
   FVNA_FIELD_STATS = 3,     /* one fvna_stats */
   FVNA_FIELD_CORNER = 4,    /* 2 binary64: the window's lower-left corner (x0, y0), moved by
                                fvna_shift */
-  FVNA_FIELD_AXIS = 5       /* nx binary64: p'/(rho0 c0^2) = q1 - 1 along row 0 (the x1 axis
+  FVNA_FIELD_AXIS = 5,      /* nx binary64: p'/(rho0 c0^2) = q1 - 1 along row 0 (the x1 axis
                                of a domain whose x2-low border is a symmetry axis, section 4.2) */
+  FVNA_FIELD_OUTFLOW = 6    /* 3 binary64: the boundary-flux budget (fvna_set_budgets) of
+                               (q1, q2, q3), summed over the steps since it was switched on */
 };
 
 /* ---- configuration ----------------------------------------------------- */
@@ -97,8 +99,10 @@ typedef struct fvna_config {
   int steps_per_graph;  /* steps captured per CUDA graph replay; 0 = default (32) */
   int tile_x;           /* x1-sweep tile width (16, 32 or 64 cells per warp row); 0 = default */
   int tile_y;           /* x2-sweep tile height (rows per warp); 0 = default */
-  int compensated;      /* FVNA_FP32_PERT: 1 = sum each cell update with error-free
-                           two-sums (one final rounding), 0 = as written */
+  int compensated;      /* FVNA_FP32_PERT: 0 = the increments of eq. fv-hr summed and added
+                           to the state in one fused multiply-add (one rounding of the sum;
+                           the default), 1 = the state and the two increments summed with
+                           error-free two-sums (each increment's product rounded first) */
   int splitting;        /* enum fvna_splitting */
   int wait_limit;       /* FVNA_FP32_PERT: polls a sweep kernel makes while it waits for one of
                            its own asynchronous tile copies before it gives up (the run then
@@ -238,6 +242,23 @@ int fvna_step_timed(fvna_ctx *ctx, float ms[3]);
 int fvna_autotune(const fvna_config *cfg, int n_domains, const fvna_domain *doms,
                   const double *const *q0, int q0_on_device, void *stream, int trial_steps,
                   fvna_config *best, float *ms_per_step);
+
+/* fvna_set_budgets -- switch the per-step boundary-flux budget on (1) or off
+ * (0) for every domain of the context.  On, each step runs one small binary64
+ * kernel before each sweep that adds dt/dx times the net numerical flux out
+ * through the two border faces of every line, Fh(n-1/2) - Fh(-1/2) with
+ * Fh(-1/2) = f(Q_0) - A+dQ + F~ and Fh(n-1/2) = f(Q_{n-1}) + A-dQ + F~ (eqs.
+ * fv-hr, fluc:m, fluc:p, limiter): the sum of eq. fv-hr over a line's cells
+ * telescopes to that difference because the fluctuations of an inner face
+ * add up to the flux difference (eq. RoeCond).  With periodic and
+ * zero-order-extrapolation borders the source's Laplacian sums to zero, so
+ * FVNA_FIELD_BUDGET(t) = FVNA_FIELD_BUDGET(t_on) - FVNA_FIELD_OUTFLOW(t) up to
+ * rounding; a reflective border adds the viscous momentum flux into the
+ * wall, and the axisymmetric form its geometric volume terms, which the
+ * budget does not hold.  Switching on resets the sums to zero; either way
+ * the step graph is captured again on the next step.  FVNA_ERR_ARG for a
+ * NULL context or another value of on. */
+int fvna_set_budgets(fvna_ctx *ctx, int on);
 
 /* fvna_launch_count -- kernels this context has enqueued so far (each kernel
  * node of a graph replay counts once). */

@@ -56,7 +56,7 @@ def convergence_rate(etas, errors) -> float:
 
 def focused_axis_run(solver, dx: float, t1: float, t_end: float, probe_x1: float,
                      lab_cells: int, extrapolate_side: int = 0, from_bc: int = 1,
-                     velocity: float = 1.0):
+                     velocity: float = 1.0, central: bool = False):
     """The two stages of section 4.2 on a fvna.Solver holding one domain whose
     x2-low border is the symmetry axis: step by step until t1 with the domain
     at rest; then the driven x1-low border becomes a zero-order extrapolation
@@ -65,8 +65,14 @@ def focused_axis_run(solver, dx: float, t1: float, t_end: float, probe_x1: float
     updates the running maximum of each lab-frame cell (the on-axis pressure
     maxima of the section) and the pressure at the lab point (probe_x1, 0) is
     recorded.  Returns (axis maxima over lab cells 0..lab_cells-1, times,
-    probe pressures)."""
+    probe pressures); with central=True also the maxima of the packet's
+    central peak (section 4.2 measures the maximum pressure on the central
+    peak of the packet, away from its transitory head and tail): at each lab
+    cell the maximum over the one period centred on the passage of the
+    packet's centre, which on the axis reaches x1 at t = x1 (tau = t - x1 in
+    eq. hifuBC), i.e. over |t - x1| <= 1/2."""
     lab = np.full(lab_cells, -np.inf)
+    cen = np.full(lab_cells, -np.inf)
     times, probe = [], []
     switched, moved = False, 0
     t = solver.stats(0)["t"]
@@ -86,10 +92,17 @@ def focused_axis_run(solver, dx: float, t1: float, t_end: float, probe_x1: float
         n = min(len(p), lab_cells - k0)
         if n > 0:
             np.maximum(lab[k0:k0 + n], p[:n], out=lab[k0:k0 + n])
+            if central:
+                x = (np.arange(k0, k0 + n) + 0.5) * dx
+                inside = np.abs(t - x) <= 0.5
+                cen[k0:k0 + n] = np.where(inside, np.maximum(cen[k0:k0 + n], p[:n]),
+                                          cen[k0:k0 + n])
         ip = int(math.floor(probe_x1 / dx)) - k0
         if 0 <= ip < len(p):
             times.append(t)
             probe.append(p[ip])
+    if central:
+        return lab, np.asarray(times), np.asarray(probe), cen
     return lab, np.asarray(times), np.asarray(probe)
 
 

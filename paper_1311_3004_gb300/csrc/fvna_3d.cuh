@@ -193,46 +193,58 @@ __device__ __forceinline__ float ratio(float a, float b) { return __fdividef(a, 
 
 // Fluctuations (eqs. fluc:m, fluc:p) and limited correction flux (eq.
 // limiter) of face I, with its left and right neighbour faces for the upwind
-// ratio theta (full four-component dot products).
+// ratio theta (full four-component dot products).  The waves W[p][k] = a_p
+// r_p have structural zeros (families 3 and 4 carry one component each, the
+// acoustic families all four); the sums below leave out the products with
+// those zeros, which changes no value (x + 0 = x, and the binary64 order of
+// the remaining terms is that of the full sums), and each family reads only
+// its own wave of the upwind face.
+template <int LIM, class T>
+__device__ __forceinline__ T coef_of(T s, T wdotw, T wup, T lam) {
+  T theta = wdotw > T(0) ? ratio(wup, wdotw) : T(0);
+  T phi = wdotw > T(0) ? limiter_phi<LIM, T>(theta) : T(0);
+  T as = fabs(s);
+  return as * (T(1) - lam * as) * phi;
+}
 template <int LIM, class T>
 __device__ __forceinline__ void flux4(const Face4<T> &I, const Face4<T> &Lf, const Face4<T> &Rf,
                                       T lam, T am[4], T ap[4], T F[4]) {
-  T W[4][4];
-  waves(I, W);
-  const T s[4] = {I.s0, I.s1, I.u, I.u};
-#pragma unroll
-  for (int k = 0; k < 4; k++) {
-    T m = T(0), p = T(0);
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      T sm = s[q] < T(0) ? s[q] : T(0);
-      T sp = s[q] > T(0) ? s[q] : T(0);
-      m = m + sm * W[q][k];
-      p = p + sp * W[q][k];
-    }
-    am[k] = m;
-    ap[k] = p;
-  }
-  T coef[4];
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    T U[4][4];
-    waves(s[q] > T(0) ? Lf : Rf, U);
-    T wdotw = T(0), wup = T(0);
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      wdotw = wdotw + W[q][k] * W[q][k];
-      wup = wup + U[q][k] * W[q][k];
-    }
-    T theta = wdotw > T(0) ? ratio(wup, wdotw) : T(0);
-    T phi = wdotw > T(0) ? limiter_phi<LIM, T>(theta) : T(0);
-    T as = fabs(s[q]);
-    coef[q] = as * (T(1) - lam * as) * phi;
-  }
-#pragma unroll
-  for (int k = 0; k < 4; k++)
-    F[k] = T(0.5) * (coef[0] * W[0][k] + coef[1] * W[1][k] + coef[2] * W[2][k] +
-                     coef[3] * W[3][k]);
+  // waves of this face, acoustic families 0 and 1
+  const T W00 = I.a1, W01 = I.a1 * I.s0, W02 = I.a1 * I.r13, W03 = I.a1 * I.r14;
+  const T W10 = I.a2, W11 = I.a2 * I.s1, W12 = I.a2 * I.r23, W13 = I.a2 * I.r24;
+  const T s0 = I.s0, s1 = I.s1, u = I.u;
+  const T sm0 = s0 < T(0) ? s0 : T(0), sp0 = s0 > T(0) ? s0 : T(0);
+  const T sm1 = s1 < T(0) ? s1 : T(0), sp1 = s1 > T(0) ? s1 : T(0);
+  const T smu = u < T(0) ? u : T(0), spu = u > T(0) ? u : T(0);
+  // sum over the families in the order 0, 1, 2, 3 of s^- W (s^+ W)
+  am[0] = (T(0) + sm0 * W00) + sm1 * W10;
+  ap[0] = (T(0) + sp0 * W00) + sp1 * W10;
+  am[1] = (T(0) + sm0 * W01) + sm1 * W11;
+  ap[1] = (T(0) + sp0 * W01) + sp1 * W11;
+  am[2] = ((T(0) + sm0 * W02) + sm1 * W12) + smu * I.a3;
+  ap[2] = ((T(0) + sp0 * W02) + sp1 * W12) + spu * I.a3;
+  am[3] = ((T(0) + sm0 * W03) + sm1 * W13) + smu * I.a4;
+  ap[3] = ((T(0) + sp0 * W03) + sp1 * W13) + spu * I.a4;
+  // the upwind face's wave of each family (values selected, so that the
+  // faces stay in registers)
+  const bool l0 = s0 > T(0), l1 = s1 > T(0), lu = u > T(0);
+  const T ua1 = l0 ? Lf.a1 : Rf.a1, us0 = l0 ? Lf.s0 : Rf.s0;
+  const T ur13 = l0 ? Lf.r13 : Rf.r13, ur14 = l0 ? Lf.r14 : Rf.r14;
+  const T ua2 = l1 ? Lf.a2 : Rf.a2, us1 = l1 ? Lf.s1 : Rf.s1;
+  const T ur23 = l1 ? Lf.r23 : Rf.r23, ur24 = l1 ? Lf.r24 : Rf.r24;
+  const T ua3 = lu ? Lf.a3 : Rf.a3, ua4 = lu ? Lf.a4 : Rf.a4;
+  const T V00 = ua1, V01 = ua1 * us0, V02 = ua1 * ur13, V03 = ua1 * ur14;
+  const T V10 = ua2, V11 = ua2 * us1, V12 = ua2 * ur23, V13 = ua2 * ur24;
+  const T c0 = coef_of<LIM, T>(s0, (((T(0) + W00 * W00) + W01 * W01) + W02 * W02) + W03 * W03,
+                               (((T(0) + V00 * W00) + V01 * W01) + V02 * W02) + V03 * W03, lam);
+  const T c1 = coef_of<LIM, T>(s1, (((T(0) + W10 * W10) + W11 * W11) + W12 * W12) + W13 * W13,
+                               (((T(0) + V10 * W10) + V11 * W11) + V12 * W12) + V13 * W13, lam);
+  const T c2 = coef_of<LIM, T>(u, T(0) + I.a3 * I.a3, T(0) + ua3 * I.a3, lam);
+  const T c3 = coef_of<LIM, T>(u, T(0) + I.a4 * I.a4, T(0) + ua4 * I.a4, lam);
+  F[0] = T(0.5) * (c0 * W00 + c1 * W10);
+  F[1] = T(0.5) * (c0 * W01 + c1 * W11);
+  F[2] = T(0.5) * ((c0 * W02 + c1 * W12) + c2 * I.a3);
+  F[3] = T(0.5) * ((c0 * W03 + c1 * W13) + c3 * I.a4);
 }
 
 // Cell update of eq. fv-hr.  binary64 as written; binary32 with COMP: the

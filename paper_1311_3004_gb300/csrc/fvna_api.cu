@@ -58,9 +58,12 @@ struct fvna_ctx {
   unsigned *d_ctr = nullptr;        // binary32: tile counters of the two sweeps
   int *d_redo = nullptr;            // binary32: x2-sweep tiles listed for the general split
   int redo_blocks = 1;
-  double *d_budget = nullptr;       // binary32: on-demand budget sums
+  double *d_budget = nullptr;       // on-demand budget sums (binary32, binary64 Strang)
   // moving domain: whole cells each window has moved since init (x1, x2)
   std::vector<long long> moved_x, moved_y;
+  // boundary-flux budgets (fvna_set_budgets): one small kernel before each sweep
+  int budgets = 0;
+  int max_lines = 1;
 };
 
 namespace {
@@ -161,9 +164,17 @@ int enqueue_drives(fvna_ctx *c, cudaStream_t s) {
 // speculative kernel, then the kernel that redoes the tiles it listed
 // (usually none: it returns at once)
 cudaError_t sweep_x(fvna_ctx *c, cudaStream_t s) {
+  if (c->budgets) {
+    cudaError_t e = launch_border_flux(c->cfg.precision, c->args_x, 0, c->max_lines, s);
+    if (e != cudaSuccess) return e;
+  }
   return launch_sweep_x(c->cfg.precision, c->tile_x, c->args_x, c->blocks_x, s);
 }
 cudaError_t sweep_y(fvna_ctx *c, cudaStream_t s) {
+  if (c->budgets) {
+    cudaError_t e = launch_border_flux(c->cfg.precision, c->args_y, 1, c->max_lines, s);
+    if (e != cudaSuccess) return e;
+  }
   cudaError_t e = launch_sweep_y(c->cfg.precision, c->args_y, c->blocks_y, s);
   if (e == cudaSuccess && c->cfg.precision == FVNA_FP32_PERT)
     e = launch_sweep_y_redo32(c->args_y, c->redo_blocks, s);
@@ -404,6 +415,8 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
     max_cells = std::max(max_cells, (size_t)doms[d].nx * doms[d].ny);
   }
   CK(cudaMalloc(&c->d_state, total));
+  CK(cudaMalloc(&c->d_budget, 3 * sizeof(double)));
+  for (int d = 0; d < n; d++) c->max_lines = std::max(c->max_lines, std::max(doms[d].nx, doms[d].ny));
   c->dd.resize(n);
   c->moved_x.assign(n, 0);
   c->moved_y.assign(n, 0);
@@ -464,6 +477,36 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
                     : prec == FVNA_FP32_PERT && (x == 0 || x + 2 * sw + 2 > nx || y + XROWS > ny);
         (b ? txb : tx).push_back(Tile{d, x, y, 0});
       }
+#ifndef FVNA_Y32_TALL
+#define FVNA_Y32_TALL 0   // > 0: binary32 x2 tiles mixed (experiment)
+#endif
+    if (prec == FVNA_FP32_PERT && FVNA_Y32_TALL > 0 && cfg->tile_y == 0 &&
+        ny >= 4 * c->tile_y + FVNA_Y32_TALL) {
+      // border tiles of the sweep's height first (they take the general
+      // path), then interior tiles of FVNA_Y32_TALL rows, then the interior
+      // rest in tiles of the sweep's height, so the sweep ends on short tiles
+      std::vector<Tile> tall, fill;
+      for (int x = 0; x < nx; x += ystep) {
+        const bool xb = x < 2 || x + Y32_COLS + 2 > nx;
+        int y = 0;
+        if (!xb) {
+          // the first and last tiles of an interior strip touch the x2 borders
+          tyb.push_back(Tile{d, x, 0, c->tile_y});
+          y = c->tile_y;
+          const int top = ny - c->tile_y;        // the last tile starts here
+          while (y + FVNA_Y32_TALL <= top - 2 * c->tile_y) {
+            tall.push_back(Tile{d, x, y, FVNA_Y32_TALL});
+            y += FVNA_Y32_TALL;
+          }
+          for (; y < top; y += c->tile_y) fill.push_back(Tile{d, x, y, std::min(c->tile_y, top - y)});
+          tyb.push_back(Tile{d, x, top, c->tile_y});
+        } else {
+          for (; y < ny; y += c->tile_y) tyb.push_back(Tile{d, x, y, c->tile_y});
+        }
+      }
+      ty.insert(ty.end(), tall.begin(), tall.end());
+      ty.insert(ty.end(), fill.begin(), fill.end());
+    } else
     for (int y = 0; y < ny; y += c->tile_y)
       for (int x = 0; x < nx; x += ystep) {
         bool b = prec == FVNA_FP32_PERT &&
@@ -490,7 +533,6 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
   c->blocks_y = std::max(1, std::min((c->nty + wpb - 1) / wpb, occy * sms));
   if (prec == FVNA_FP32_PERT) {
     CK(build_maps_fp32(c->dd.data(), n, c->tile_x, &c->d_maps, c->stream));
-    CK(cudaMalloc(&c->d_budget, 3 * sizeof(double)));
     CK(cudaMalloc(&c->d_ctr, 3 * sizeof(unsigned)));
     CK(cudaMemsetAsync(c->d_ctr, 0, 3 * sizeof(unsigned), c->stream));
     CK(cudaMalloc(&c->d_redo, (2 + (size_t)c->nty) * sizeof(int)));
@@ -757,10 +799,14 @@ int fvna_fields(fvna_ctx *c, int domain, int what, void *dst, size_t bytes, int 
   const DomScal &S = c->h_scal[domain];
   if (what == FVNA_FIELD_BUDGET) {
     if (bytes < 3 * sizeof(double)) return FVNA_ERR_ARG;
-    if (c->cfg.precision == FVNA_FP32_PERT) {
-      // binary32: summed on demand from the stored state, in binary64
+    if (c->cfg.precision == FVNA_FP32_PERT || c->cfg.splitting == FVNA_SPLIT_STRANG) {
+      // binary32, and binary64 Strang steps (whose sweeps end after the sum
+      // the x2 sweep accumulates): summed on demand from the stored state
       double b[3];
-      CK(launch_budget_fp32(c->dd[domain], c->d_budget, c->stream));
+      if (c->cfg.precision == FVNA_FP32_PERT)
+        CK(launch_budget_fp32(c->dd[domain], c->d_budget, c->stream));
+      else
+        CK(launch_budget_fp64(c->dd[domain], c->d_budget, c->stream));
       CK(cudaMemcpyAsync(b, c->d_budget, sizeof b, cudaMemcpyDeviceToHost, c->stream));
       CK(cudaStreamSynchronize(c->stream));
       if (dst_on_device) CK(cudaMemcpy(dst, b, sizeof b, cudaMemcpyHostToDevice));
@@ -769,6 +815,12 @@ int fvna_fields(fvna_ctx *c, int domain, int what, void *dst, size_t bytes, int 
     }
     if (dst_on_device) CK(cudaMemcpy(dst, S.budget, 3 * sizeof(double), cudaMemcpyHostToDevice));
     else std::memcpy(dst, S.budget, 3 * sizeof(double));
+    return FVNA_OK;
+  }
+  if (what == FVNA_FIELD_OUTFLOW) {
+    if (bytes < 3 * sizeof(double)) return FVNA_ERR_ARG;
+    if (dst_on_device) CK(cudaMemcpy(dst, S.outflow, 3 * sizeof(double), cudaMemcpyHostToDevice));
+    else std::memcpy(dst, S.outflow, 3 * sizeof(double));
     return FVNA_OK;
   }
   if (what == FVNA_FIELD_STATS) {
@@ -898,6 +950,23 @@ int fvna_set_correction(fvna_ctx *c, fvna_net *net, float in_scale, float out_sc
     size_t pix = (size_t)c->dd[0].nx * c->dd[0].ny;
     CK(cudaMalloc(&c->net_h, 2 * pix * 32 * sizeof(__nv_bfloat16)));
   }
+  return FVNA_OK;
+}
+
+int fvna_set_budgets(fvna_ctx *c, int on) {
+  if (!c || (on != 0 && on != 1)) return FVNA_ERR_ARG;
+  if (on) CK(launch_zero_outflow(c->args, c->stream));
+  if (on != c->budgets) {
+    // the step graph is captured again with (or without) the budget kernels
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->kernels_per_step += on ? (c->cfg.splitting == FVNA_SPLIT_STRANG ? 3 : 2)
+                              : -(c->cfg.splitting == FVNA_SPLIT_STRANG ? 3 : 2);
+    c->budgets = on;
+  }
+  CK(cudaStreamSynchronize(c->stream));
   return FVNA_OK;
 }
 

@@ -34,6 +34,11 @@ cudaError_t launch_export(int precision, const DomDev &d, double *out, int what,
 // end of a Strang step: swept planes back into the state planes (esz: bytes
 // per value), the x1 sweep's tile counter reset
 cudaError_t launch_copy_back(const StepArgs &a, int esz, cudaStream_t s);
+// boundary-flux budget of a sweep (dir 0: x1 sweep, before it; dir 1: x2
+// sweep, before it), binary64, added to every domain's outflow; and its reset
+cudaError_t launch_border_flux(int precision, const StepArgs &a, int dir, int max_lines,
+                               cudaStream_t s);
+cudaError_t launch_zero_outflow(const StepArgs &a, cudaStream_t s);
 // border rule of one side of one domain in the device descriptors
 cudaError_t launch_set_bc(DomDev *dd, int dom, int side, int bc, cudaStream_t s);
 // moving domain: shift the window of domain dom by (kx, ky) cells (two
@@ -81,6 +86,7 @@ constexpr int X32H_TILE = 60;
 constexpr int Y32_COLS = 60;
 cudaError_t build_maps_fp32(const DomDev *dd, int n, int tile_x, void **d_maps, cudaStream_t s);
 cudaError_t launch_budget_fp32(const DomDev &d, double *dst, cudaStream_t s);
+cudaError_t launch_budget_fp64(const DomDev &d, double *dst, cudaStream_t s);
 // second kernel of the binary32 x2 sweep (tiles listed for the general split)
 cudaError_t launch_sweep_y_redo32(const StepArgs &a, int blocks, cudaStream_t s);
 // ghost ring of a binary32 domain with a driven border (bytes), and the

@@ -637,8 +637,7 @@ __device__ __forceinline__ void ysink(YSrc &s, const StepArgs &A, const DomDev &
 template <int LIM, bool COMP, bool SPEC>
 __device__ __forceinline__ int y32_tile(const StepArgs &A, const DomDev &D, DomScal *S,
                                         const Maps &M, unsigned char *ring, uint64_t *bars,
-                                        unsigned &used, int x0, int y0, int lane) {
-  const int TY = A.tile_y;
+                                        unsigned &used, int x0, int y0, int TY, int lane) {
   const int nrows = TY + 2 * HALO_Y;
   const int nch = (nrows + YRB - 1) / YRB;
   const unsigned base = used;
@@ -710,10 +709,26 @@ __device__ __forceinline__ int y32_tile(const StepArgs &A, const DomDev &D, DomS
     const int r0 = y0 - HALO_Y + c * YRB;
     const bool plain_chunk = ysweep && rows == YRB && x0 >= 2 && x0 + YW + 2 <= D.nx &&
                              r0 >= 0 && r0 + YRB <= D.ny && r0 - 2 > 0;
-    // rows [0, g_end) take the general path (border rules, start of the
-    // march in the first chunk), the rest the plain one
+    // rows [0, g_end) take the start of the march (first chunk) or the
+    // general path (border rules), the rest the plain loop; in a plain
+    // chunk the start-up rows are domain cells read as they are, and every
+    // face they make is a domain face, so no border rule or accounting mask
+    // applies to them either
     const int g_end = plain_chunk ? (c == 0 ? 4 : 0) : rows;
-    for (int i = 0; i < g_end; i++) {
+    if (plain_chunk) {
+      for (int i = 0; i < g_end; i++) {
+        const int j = c * YRB + i;
+        const unsigned char *rp = st + i * (YBOX * 4) + (2 + 2 * lane) * 4;
+        Cell q;
+        q.a = *(const float2 *)(rp);
+        q.c = *(const float2 *)(rp + YRB * YBOX * 4);
+        q.b = *(const float2 *)(rp + 2 * YRB * YBOX * 4);
+        if (m.template push<false>(j, q, out, true, true, true, true, false))
+          ysink<false>(src, A, D, x0, y0, TY, lane, y0 - HALO_Y + j - 2, out.a, out.c, out.b,
+                       source, axi, coef, dt32, ca, cb, qo);
+      }
+    }
+    for (int i = plain_chunk ? g_end : 0; i < g_end; i++) {
       const int j = c * YRB + i;
       Cell q = fetch(i, j);
       if (!ysweep) {
@@ -817,10 +832,12 @@ __global__ void __launch_bounds__(32, Y32_MINBLOCKS) k_sweep_y32(StepArgs A) {
     const int x0 = tl.x0, y0 = tl.y0;
     // one code path for all tiles (border rules are per-row branches that
     // chunks away from the domain edges skip)
+    // a tile's height: its own (the host may mix heights), else the sweep's
+    const int TY = tl.pad > 0 ? tl.pad : A.tile_y;
     int rc = REDO ? x2::y32_tile<LIM, COMP, false>(A, D, S, maps[tl.dom], ring, bars, used, x0,
-                                                    y0, lane)
+                                                    y0, TY, lane)
                   : x2::y32_tile<LIM, COMP, true>(A, D, S, maps[tl.dom], ring, bars, used, x0, y0,
-                                                   lane);
+                                                   TY, lane);
     if (rc == 2 && lane == 0) A.redo[A.redo_off + atomicAdd(&A.redo[1], 1)] = w;
     if (rc == 1) break;
     it = REDO ? cur + (int)gridDim.x : take_tile_collect(tn);

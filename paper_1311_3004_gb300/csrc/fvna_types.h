@@ -55,9 +55,13 @@ struct DomScal {
   // per-step constants derived from dt (set wherever dt is set)
   double lam, coef;              // dt/dx and dt*delta/dx^2
   float lam32, coef32, dt32, pad32;
+  // binary64 boundary-flux budget (fvna_set_budgets): sum over the sweeps of
+  // dt/dx times the net numerical flux out through the domain's border faces
+  double outflow[3];
 };
 
-// One warp's work item: domain and the tile origin (cells).
+// One warp's work item: domain, the tile origin (cells) and, for the
+// binary32 x2 sweep, the tile's height (0: the sweep's tile_y).
 struct Tile {
   int dom, x0, y0, pad;
 };

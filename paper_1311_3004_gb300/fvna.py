@@ -24,6 +24,7 @@ LIM_MC, LIM_NONE, LIM_LW = 0, 1, 2
 SPLIT_GODUNOV, SPLIT_STRANG = 0, 1
 BC_PERIODIC, BC_EXTRAP, BC_REFLECT, BC_TAYLOR, BC_HIFU = 0, 1, 2, 3, 4
 FIELD_Q, FIELD_PRESSURE, FIELD_BUDGET, FIELD_STATS, FIELD_CORNER, FIELD_AXIS = 0, 1, 2, 3, 4, 5
+FIELD_OUTFLOW = 6
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONREAL, ERR_CFL, ERR_NAN = 0, -1, -2, -3, -4, -5, -6
 ERR_SIZE = -7
@@ -81,7 +82,7 @@ SYMBOLS = ["fvna_init", "fvna_step", "fvna_run", "fvna_sync", "fvna_fields",
            "fvna_last_cuda_error",
            "fvna_step_noalloc", "fvna_autotune", "fvna_net_create", "fvna_net_params",
            "fvna_net_forward", "fvna_net_backward", "fvna_net_train_step", "fvna_net_destroy",
-           "fvna_set_correction", "fvna3_init", "fvna3_run", "fvna3_step_timed", "fvna3_fields",
+           "fvna_set_correction", "fvna_set_budgets", "fvna3_init", "fvna3_run", "fvna3_step_timed", "fvna3_fields",
            "fvna3_launch_count", "fvna3_destroy"]
 
 _lib = None
@@ -153,6 +154,8 @@ def lib():
     L.fvna_step_noalloc.restype = ctypes.c_int
     L.fvna_step_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Domain), vp, vp,
                                     ctypes.c_double, ctypes.c_double, dp, vp]
+    L.fvna_set_budgets.restype = ctypes.c_int
+    L.fvna_set_budgets.argtypes = [vp, ctypes.c_int]
     L.fvna3_init.restype = ctypes.c_int
     L.fvna3_init.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Domain3), vp, ctypes.c_int, vp,
                              ctypes.POINTER(vp)]
@@ -187,7 +190,7 @@ def _check(rc: int, where: str) -> int:
 
 def make_config(precision=FP64, geometry=CARTESIAN, limiter=LIM_MC, sweeps=7, beta=3.5,
                 delta=0.0, dx=1.0, nu_w=0.9, nu_max=1.0, dt_fixed=0.0, steps_per_graph=0,
-                tile_x=0, tile_y=0, compensated=1, splitting=0, wait_limit=0) -> Config:
+                tile_x=0, tile_y=0, compensated=0, splitting=0, wait_limit=0) -> Config:
     return Config(precision, geometry, limiter, sweeps, beta, delta, dx, nu_w, nu_max, dt_fixed,
                   steps_per_graph, tile_x, tile_y, compensated, splitting, wait_limit)
 
@@ -425,6 +428,17 @@ class Solver:
         arr = np.zeros(3, dtype=np.float64)
         _check(lib().fvna_fields(self._h, domain, FIELD_BUDGET, ctypes.c_void_p(arr.ctypes.data),
                                  arr.nbytes, 0), "fvna_fields")
+        return arr
+
+    def set_budgets(self, on: bool = True) -> None:
+        """Per-step boundary-flux budget on or off (fvna_set_budgets; on resets it)."""
+        _check(lib().fvna_set_budgets(self._h, int(bool(on))), "fvna_set_budgets")
+
+    def outflow(self, domain: int = 0):
+        """Boundary-flux budget of (q1, q2, q3) since it was switched on."""
+        arr = np.zeros(3, dtype=np.float64)
+        _check(lib().fvna_fields(self._h, domain, FIELD_OUTFLOW,
+                                 ctypes.c_void_p(arr.ctypes.data), arr.nbytes, 0), "fvna_fields")
         return arr
 
     def corner(self, domain: int = 0):

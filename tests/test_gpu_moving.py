@@ -10,11 +10,11 @@ the Taylor-shock study of section 4.1 (Table tab:error-ts) run on it.
 - a moving window that follows the shock to t = 100 reproduces the paper's
   error table at theta_T = 0: E_1 falls with eta at an order above one and
   lies at eta = 82 within a factor of three of the printed best..worst range.
-  At the rotated angles the errors fall at first order and stay within a
-  factor of ten of the printed range: there they are set by the analytic
-  Dirichlet borders that cut the shock front (the paper's borders, with a
-  window size it does not give), and shrink as the window widens across the
-  propagation direction.
+  At the rotated angles the analytic Dirichlet borders (the paper's) cut the
+  shock front and set the error, which shrinks as the window widens across
+  the propagation direction; on windows 100 units wide (the paper ran its
+  moving domains 100 wavelengths long) the rotated errors converge at the
+  paper's order or above and stay below three times its worst values.
 """
 import math
 import os
@@ -151,24 +151,44 @@ def taylor_moving_errors(angle, eta, nu_w=0.9, t_end=100.0, ratio=1e-7, beta=3.5
 
 @pytest.mark.parametrize("k", [0, 32, 16, 8, 4])
 def test_taylor_table_on_a_moving_window(k):
+    """Table tab:error-ts, nu_W = 0.9.  theta_T = 0 on a 30-unit quasi-1D
+    window, eta up to 82: the paper's order and error range (within three
+    times).  Rotated shocks on square windows 100 units wide (the paper ran
+    its moving domains 100 wavelengths long), eta = 10, 20, 41: at least the
+    paper's lowest rate (1.15), and errors at eta = 41 no worse than three
+    times the paper's worst at eta = 82 (finer grids only lower them; on
+    windows this wide the rotated errors are below the paper's)."""
     angle = 0.0 if k == 0 else math.pi / k
     tab = _paper_table()
-    etas = [10, 20, 41, 82]
-    res = [taylor_moving_errors(angle, eta) for eta in etas]
+    etas = [10, 20, 41, 82] if k == 0 else [10, 20, 41]
+    res = [taylor_moving_errors(angle, eta, side=100.0) for eta in etas]
     e1 = np.array([r[0] for r in res])
     einf = np.array([r[1] for r in res])
     print(f"theta=pi/{k}: E1 {e1}, Einf {einf}")
     rate1 = analysis.convergence_rate(etas, e1)
     assert np.all(np.diff(e1) < 0), e1
     assert np.all(np.diff(einf) < 0), einf
-    # theta_T = 0: the paper's second order and error range; rotated: first
-    # order, within ten times the range (module docstring)
-    min_rate, factor = (1.5, 3.0) if k == 0 else (0.85, 10.0)
-    assert rate1 > min_rate, rate1
-    best, worst = tab[(angle, "E1")][4], tab[(angle, "E1")][5]
-    assert best / factor <= e1[-1] <= factor * worst, (e1[-1], best, worst)
-    best, worst = tab[(angle, "Einf")][4], tab[(angle, "Einf")][5]
-    assert best / factor <= einf[-1] <= factor * worst, (einf[-1], best, worst)
+    best1, worst1 = tab[(angle, "E1")][4], tab[(angle, "E1")][5]
+    besti, worsti = tab[(angle, "Einf")][4], tab[(angle, "Einf")][5]
+    if k == 0:
+        assert rate1 > 1.5, rate1
+        assert best1 / 3.0 <= e1[-1] <= 3.0 * worst1, (e1[-1], best1, worst1)
+        assert besti / 3.0 <= einf[-1] <= 3.0 * worsti, (einf[-1], besti, worsti)
+    else:
+        assert rate1 >= 1.15, rate1
+        assert e1[-1] <= 3.0 * worst1, (e1[-1], worst1)
+        assert einf[-1] <= 3.0 * worsti, (einf[-1], worsti)
     for r in res:
         # the paper's CFL spread: nu never further than 1e-8 from its mean
         assert r[2]["nu_std"] < 1e-8
+
+
+def test_rotated_taylor_error_is_set_by_the_window_extent():
+    """The analytic values on the window's borders cut the rotated shock front
+    and set its error: at theta_T = pi/8, eta = 20, a 100-unit window has an
+    E_1 several times below a 12-unit one, and converges at second order
+    where the 12-unit one converges at first."""
+    small = [taylor_moving_errors(math.pi / 8, eta, side=12.0)[0] for eta in (10, 20)]
+    wide = [taylor_moving_errors(math.pi / 8, eta, side=100.0)[0] for eta in (10, 20)]
+    assert wide[1] < small[1] / 5.0, (small, wide)
+    assert np.log2(small[0] / small[1]) < 1.3 and np.log2(wide[0] / wide[1]) > 1.7, (small, wide)
