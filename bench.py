@@ -260,12 +260,21 @@ _TRAFFIC_KEYS = [
     (r"k_sweep_x<(fvna::)?P64", "k_sweep_x_fp64"),
     (r"k_sweep_y<(fvna::)?P64", "k_sweep_y_fp64"),
 ]
+# the 3D kernels (k3_sweep_v serves the x2 and the x3 sweep: one figure for both)
+_TRAFFIC_KEYS3 = [
+    (r"k3_sweep_x<float", "k3_sweep_x_fp32"), (r"k3_sweep_v<float", "k3_sweep_v_fp32"),
+    (r"k3_source<float", "k3_source_fp32"), (r"k3_sweep_x<double", "k3_sweep_x_fp64"),
+    (r"k3_sweep_v<double", "k3_sweep_v_fp64"), (r"k3_source<double", "k3_source_fp64"),
+]
 
 
-def record_traffic(csv_path: str, out_path: str, n: int = N_SIDE) -> dict:
+def record_traffic(csv_path: str, out_path: str, n: int = N_SIDE, n3: int = 256) -> dict:
     """DRAM bytes per launch of each sweep from an ncu CSV capture of
-    `bench.py` on the n x n pulse, keyed to the digest of the kernel sources
-    this script sees (a capture taken on other sources is never matched)."""
+    `bench.py` on the n x n pulse (and of the 3D kernels on the n3^3 pulse,
+    if the capture holds them), keyed to the digest of the kernel sources
+    this script sees (a capture taken on other sources is never matched).
+    Figures already in out_path for kernels the capture does not hold are
+    kept."""
     import csv
     import re
     rows = [r for r in csv.reader(open(csv_path)) if r]
@@ -289,6 +298,20 @@ def record_traffic(csv_path: str, out_path: str, n: int = N_SIDE) -> dict:
                      "while the kernel sources hash to source_digest (written by bench.py "
                      "--record-traffic, never by hand)")}
     digest = source_digest()
+    try:
+        old = json.load(open(out_path))
+        for k, v in old.items():
+            if k != "_note":
+                out[k] = v
+    except Exception:
+        pass
+    for pat, key in _TRAFFIC_KEYS3:
+        ids = [k for k in per_launch if re.search(pat, k[1])]
+        if ids:
+            out[f"{key}_{n3}"] = {"dram_bytes_per_launch":
+                                  int(round(sum(per_launch[k] for k in ids) / len(ids))),
+                                  "launches": len(ids),
+                                  "source_digest": source_digest(_SWEEP3_SOURCES)}
     for pat, key in _TRAFFIC_KEYS:
         # launches in capture order; the x2 sweep's second kernel follows its first
         ids = [k for k in per_launch if re.search(pat, k[1])]
@@ -873,7 +896,7 @@ def run_learned(args):
     (net, info), train_s = _timed(torch, lambda: learned.train_net(X, T, steps=4000, crop=128,
                                                                   batch=8, lr=5e-4, noise=0.05,
                                                                   importance=True, log=log))
-    res = learned.evaluate(spec, 0.35e6, net, info, gains=(1.0, 0.5))
+    res = learned.evaluate(spec, 0.35e6, net, info, gains=(1.0, 0.5), fine32=True)
     net.close()
     cells_c = spec.nz * spec.nr
     c, cn = res["coarse"], res["coarse_net"]
@@ -882,6 +905,7 @@ def run_learned(args):
             "time_to_solution_s": cn["seconds"],
             "fine_fp64_time_to_solution_s": res["fine_seconds"],
             "speedup_vs_fine_fp64": res["fine_seconds"] / cn["seconds"],
+            "fine_fp32": res.get("fine_fp32"),
             "focal_peak_rel_err": cn["focal_peak_rel_err"], "l2_rel_err": cn["l2_rel_err"],
             "status": cn.get("status", 0),
             "gain_0.5": res.get("coarse_net_gain0.5"),
@@ -896,12 +920,15 @@ def run_learned(args):
 
 def run_netfwd(args):
     """Inference throughput of the correction network (three BF16 tensor-core
-    convolutions) on one 2048x512 coarse field, CUDA-event timed."""
+    convolutions) on 2048x512 coarse fields, CUDA-event timed; eight fields per
+    call, so the wrapper's synchronisation at the end of each call is paid
+    once per eight fields (inside a corrected run the network is a graph node
+    and nothing synchronises)."""
     torch, fvna = _setup_cuda()
     from paper_1311_3004_gb300 import learned
-    H, W = 512, 2048
+    H, W, B = 512, 2048, 8
     net = fvna.Net(learned._init_params(0))
-    x = torch.randn((1, 3, H, W), dtype=torch.float32, device="cuda")
+    x = torch.randn((B, 3, H, W), dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         net.forward(x)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -910,7 +937,7 @@ def run_netfwd(args):
         net.forward(x)
     ev[1].record()
     torch.cuda.synchronize()
-    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    ms = ev[0].elapsed_time(ev[1]) / args.steps / B
     flops = 2.0 * 9 * (3 * 32 + 32 * 32 + 32 * 3) * H * W    # algorithmic multiply-adds x 2
     pk, kind = peaks()
     print(json.dumps({"metric": "TFLOP/s", "workload": "net_forward_2048x512", "dtype": "bf16",
@@ -918,7 +945,9 @@ def run_netfwd(args):
                       "roofline": {"bound": "tensor", "peak": pk["bf16_tflops"],
                                    "frac": flops / (ms * 1e-3) / 1e12 / pk["bf16_tflops"],
                                    "peak_source": kind},
-                      "note": "includes the host-synchronising wrapper per forward"}), flush=True)
+                      "fields_per_call": B,
+                      "note": "per field; the wrapper synchronises once per call of 8 fields"}),
+          flush=True)
     net.close()
     return 0
 
@@ -926,7 +955,7 @@ def run_netfwd(args):
 def main():
     args = parse()
     if args.record_traffic:
-        print(json.dumps(record_traffic(args.record_traffic, args.traffic_out, args.n)))
+        print(json.dumps(record_traffic(args.record_traffic, args.traffic_out, args.n, args.n3)))
         return 0
     if args.workload == "netfwd":
         return run_netfwd(args)

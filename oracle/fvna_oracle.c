@@ -3,7 +3,7 @@
  * Velasco-Segura & Rendon, "A Finite Volume Approach for the Simulation of
  * Nonlinear Dissipative Acoustic Wave Propagation" (arXiv 1311.3004).
  *
- * TEST INFRASTRUCTURE ONLY.  This file is the checker the GPU library is
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle the GPU library is
  * compared against.  Only the test suite, the smoke check and the benchmark's
  * CPU-baseline leg may load it.  It shares no code, header, table or helper
  * with the CUDA library, and the library never calls it.

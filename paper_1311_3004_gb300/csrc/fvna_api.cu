@@ -352,19 +352,13 @@ static int pick_tile_x32(int n, const fvna_domain *d, int sms) {
   return best;
 }
 // x2 sweep: each warp marches its columns row after row, so the sweep runs
-// at the pace of its warps' latency; heights whose marched rows (ty + 6)
-// fill whole 8-row chunks, the largest that still gives every resident warp
-// (about 12 per SM) two tiles.
-static int pick_tile_y32(int n, const fvna_domain *d, int sms) {
-  int best = 10;
-  for (int ty = 10; ty <= 250; ty += 8) {
-    long long T = 0;
-    for (int k = 0; k < n; k++)
-      T += (long long)((d[k].nx + Y32_COLS - 1) / Y32_COLS) * ((d[k].ny + ty - 1) / ty);
-    if (T >= 2LL * 12 * sms) best = ty;
-  }
-  return best;
-}
+// at the pace of its warps' latency and of its slowest tiles (those at a
+// border take the general path); a height whose marched rows (ty + 6) fill
+// whole 8-row chunks.  The smallest, 10 (two chunks, both loaded when the
+// tile starts, and the most tiles to balance the warps with), measured
+// fastest on the 2048^2 pulse (53.6 us against 56.2 for 18 and 68.7 for 22;
+// taller tiles and mixed heights were slower still).
+static int pick_tile_y32() { return 10; }
 
 static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
                      const double *const *q0, int q0_on_device, void *stream, fvna_ctx *c) {
@@ -383,7 +377,7 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
     c->tile_y = cfg->tile_y ? cfg->tile_y : 64;
   } else {
     c->tile_x = cfg->tile_x ? cfg->tile_x : pick_tile_x32(n, doms, sms);
-    c->tile_y = cfg->tile_y ? cfg->tile_y : pick_tile_y32(n, doms, sms);
+    c->tile_y = cfg->tile_y ? cfg->tile_y : pick_tile_y32();
   }
   // border values evaluated once per step: binary64 domains driven on the
   // x1-low border (HIFU) keep a drive buffer; binary32 domains with any
@@ -477,36 +471,6 @@ static int init_impl(const fvna_config *cfg, int n, const fvna_domain *doms,
                     : prec == FVNA_FP32_PERT && (x == 0 || x + 2 * sw + 2 > nx || y + XROWS > ny);
         (b ? txb : tx).push_back(Tile{d, x, y, 0});
       }
-#ifndef FVNA_Y32_TALL
-#define FVNA_Y32_TALL 0   // > 0: binary32 x2 tiles mixed (experiment)
-#endif
-    if (prec == FVNA_FP32_PERT && FVNA_Y32_TALL > 0 && cfg->tile_y == 0 &&
-        ny >= 4 * c->tile_y + FVNA_Y32_TALL) {
-      // border tiles of the sweep's height first (they take the general
-      // path), then interior tiles of FVNA_Y32_TALL rows, then the interior
-      // rest in tiles of the sweep's height, so the sweep ends on short tiles
-      std::vector<Tile> tall, fill;
-      for (int x = 0; x < nx; x += ystep) {
-        const bool xb = x < 2 || x + Y32_COLS + 2 > nx;
-        int y = 0;
-        if (!xb) {
-          // the first and last tiles of an interior strip touch the x2 borders
-          tyb.push_back(Tile{d, x, 0, c->tile_y});
-          y = c->tile_y;
-          const int top = ny - c->tile_y;        // the last tile starts here
-          while (y + FVNA_Y32_TALL <= top - 2 * c->tile_y) {
-            tall.push_back(Tile{d, x, y, FVNA_Y32_TALL});
-            y += FVNA_Y32_TALL;
-          }
-          for (; y < top; y += c->tile_y) fill.push_back(Tile{d, x, y, std::min(c->tile_y, top - y)});
-          tyb.push_back(Tile{d, x, top, c->tile_y});
-        } else {
-          for (; y < ny; y += c->tile_y) tyb.push_back(Tile{d, x, y, c->tile_y});
-        }
-      }
-      ty.insert(ty.end(), tall.begin(), tall.end());
-      ty.insert(ty.end(), fill.begin(), fill.end());
-    } else
     for (int y = 0; y < ny; y += c->tile_y)
       for (int x = 0; x < nx; x += ystep) {
         bool b = prec == FVNA_FP32_PERT &&

@@ -190,9 +190,11 @@ def train_net(X, T, steps=1500, batch=8, crop=96, lr=1e-3, margin=4, seed=0, noi
 
 
 def evaluate(spec: Spec, p_surface: float, net=None, info=None, fine_precision=fvna.FP64,
-             t_end=None, gains=(1.0,)):
+             t_end=None, gains=(1.0,), fine32=False):
     """Run coarse (with and without the network) and fine to t_end; return the
-    focal peak pressures, errors against the fine run and the run times."""
+    focal peak pressures, errors against the fine run and the run times;
+    with fine32 also the fine grid in binary32 (the fastest plain solver of
+    the same accuracy) against the same reference."""
     import torch
     t_end = spec.t_end if t_end is None else t_end
     out = {}
@@ -224,6 +226,19 @@ def evaluate(spec: Spec, p_surface: float, net=None, info=None, fine_precision=f
     peak_f = float(pfr.max())
     res = {"t_end": t_end, "p_surface": p_surface, "focal_peak_fine": peak_f,
            "fine_seconds": out["fine"]["seconds"]}
+    if fine32:
+        s, w = _solver(spec, True, p_surface, precision=fvna.FP32_PERT, steps_per_graph=64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = s.run(t_end=t_end, check=False)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        p32 = restrict(torch, _pert(torch, torch.from_numpy(s.q(0)).cuda()), dxf)[0].cpu().double()
+        s.close()
+        res["fine_fp32"] = {"seconds": sec, "status": st["rc"],
+                            "focal_peak_rel_err": abs(float(p32.max()) - peak_f) / peak_f,
+                            "l2_rel_err": float(torch.linalg.norm(p32 - pfr) /
+                                                torch.linalg.norm(pfr))}
     for name in out:
         if name == "fine":
             continue
