@@ -61,12 +61,13 @@ def parse():
                     default="gaussian",
                     help="gaussian: the headline line; the others print their own line")
     ap.add_argument("--n3", type=int, default=256, help="side of the 3D pulse workload")
-    ap.add_argument("--taylor-extent", type=float, default=12.0,
-                    help="side of the square window of the rotated Taylor shocks (units of x)")
+    ap.add_argument("--taylor-extent", type=float, default=100.0,
+                    help="side of the square window of the rotated Taylor shocks (units of x; "
+                         "the paper's domains are 100 wavelengths long)")
     ap.add_argument("--taylor-angles", default="0,32,16,8,4",
                     help="theta_T = pi/k for these k (0: theta_T = 0)")
-    ap.add_argument("--taylor-etas", default="5,10,20,41,82",
-                    help="eta of the rotated shocks")
+    ap.add_argument("--taylor-etas", default="5,10,20,41",
+                    help="eta of the rotated shocks (82 on a 100-unit window: about 10 min a run)")
     ap.add_argument("--taylor-etas0", default="5,10,20,41,82", help="eta of theta_T = 0")
     ap.add_argument("--taylor-nus", default="0.6,0.7,0.8,0.9,0.99")
     ap.add_argument("--hifu-nus", default="0.6,0.7,0.8,0.9,0.99")

@@ -32,8 +32,11 @@
 namespace fvna {
 
 constexpr int X32_ROWS = 32;
+// resident x1-sweep warps per SM the register allocator plans for: 12 gives
+// the speculative march 168 registers (a few spilled bytes) and lets the
+// 32-cell tiles (16 KB of shared memory) keep 12 warps per SM
 #ifndef X32_MINBLOCKS
-#define X32_MINBLOCKS 1
+#define X32_MINBLOCKS 12
 #endif
 #ifndef FVNA_Y_UNROLL
 #define FVNA_Y_UNROLL 2   // rows of the x2 sweep's plain loop unrolled together (measured best)
@@ -376,6 +379,17 @@ __device__ __forceinline__ bool x32_tile(const StepArgs &A, const DomDev &D, Dom
 
 }  // namespace x2
 
+// The general split of a tile, kept out of line: it needs more registers
+// than the speculative march, and inlined it would set the register count
+// (and so the resident warps) of the whole kernel; called for the rare tile
+// that meets a face that is not subsonic, it may spill.
+template <int SW, int LIM, bool COMP>
+__device__ __noinline__ void x32_general(const StepArgs &A, const DomDev &D, DomScal *S,
+                                         unsigned char *mainb, unsigned char *halo, int x0, int y0,
+                                         int lane) {
+  x2::x32_tile<SW, LIM, COMP, true, false>(A, D, S, mainb, halo, x0, y0, lane);
+}
+
 // A tile whose speculative march met a face that is not subsonic is loaded
 // again and marched with the general split by the same warp, before its
 // store: its result depends only on the state planes, which no warp of the
@@ -450,7 +464,7 @@ __global__ void __launch_bounds__(32, X32_MINBLOCKS) k_sweep_x32(StepArgs A) {
           break;
         }
         phase ^= 1;
-        x2::x32_tile<SW, LIM, COMP, true, false>(A, D, S, mainb, halo, x0, y0, lane);
+        x32_general<SW, LIM, COMP>(A, D, S, mainb, halo, x0, y0, lane);
       }
     }
     __syncwarp();

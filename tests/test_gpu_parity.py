@@ -361,7 +361,7 @@ def test_fp32_borders_against_fp64(bc, tile_x):
     assert peak <= 1e-5 and l2 <= 1e-5, (peak, l2)
 
 
-@pytest.mark.parametrize("tile_x", [0, 60])
+@pytest.mark.parametrize("tile_x", [0, 16, 32, 64, 60])
 @pytest.mark.parametrize("flow", [(0.75, 0.0), (0.0, 0.75)])
 def test_fp32_faces_that_are_not_subsonic(flow, tile_x):
     """A uniform flow along x1 or x2 fast enough that the second family
