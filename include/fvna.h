@@ -233,7 +233,8 @@ int fvna_step_timed(fvna_ctx *ctx, float ms[3]);
 
 /* fvna_autotune -- pick the sweep tile shapes for a set of domains.  Builds a
  * throwaway context from the same arguments as fvna_init for each candidate
- * (tile_x in {16, 32, 64}, tile_y in {8, 16, 32, 64, 128}), runs one warm-up graph of
+ * (binary64: tile_x in {16, 32, 64}, tile_y in {8, 16, 32, 64, 128}; binary32:
+ * tile_x in {16, 32, 64, 60}, tile_y in {10, 18, 26, 34, 42}), runs one warm-up graph of
  * trial_steps steps and times a second one with CUDA events on `stream`,
  * destroys it, and returns in *best a copy of *cfg with the fastest tile_x and
  * tile_y (ms_per_step, if not NULL, receives its time per step).  The

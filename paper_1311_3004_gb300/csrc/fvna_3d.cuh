@@ -93,8 +93,22 @@ template <class T> struct Face4 {
   T s0, s1, u, a1, a2, a3, a4, r13, r23, r14, r24;
 };
 
+// 1/x in binary32: the hardware approximation refined by one Newton step
+// r + r (1 - x r), within an ulp or so of the exact reciprocal and not
+// biased to one side (the approximation alone errs one way)
+__device__ __forceinline__ float rcp_nr(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ double inv_q1(double a) { return 1.0 / a; }
-__device__ __forceinline__ float inv_q1(float a) { return __frcp_rn(1.0f + a); }
+__device__ __forceinline__ float inv_q1(float a) { return rcp_nr(1.0f + a); }
 
 // Roe solver of one interface, binary64, in the order of the definitions.
 // L, R = (q1, normal momentum, transverse 1, transverse 2); zL, zR = the
@@ -134,26 +148,29 @@ __device__ __forceinline__ bool roe4(double beta, const double L[4], const doubl
 }
 
 // The same in binary32 perturbation form: Z1 - 1, D - 1 and c - 1 are carried
-// as small numbers; the reciprocals and the square root are correctly
-// rounded (a one-signed error there would bias every wave speed).
+// as small numbers.  c - 1 = (D - 1) / (1 + sqrt(D)) keeps the relative
+// precision of D - 1, so the approximate square root only touches it at the
+// 1e-7 relative level, and the reciprocals take a Newton step (a one-signed
+// error there would bias every wave speed).
 __device__ __forceinline__ bool roe4(float beta, const float L[4], const float zL[3],
                                      const float R[4], const float zR[3], Face4<float> &F) {
   float Z1p = 0.5f * (L[0] + R[0]);
   float Z2 = 0.5f * (zL[0] + zR[0]);
   float Z3 = 0.5f * (zL[1] + zR[1]);
   float Z4 = 0.5f * (zL[2] + zR[2]);
-  float rZ1 = __frcp_rn(1.0f + Z1p);
+  float rZ1 = rcp_nr(1.0f + Z1p);
   float u = Z2 * rZ1;
   float v = Z3 * rZ1;
   float w = Z4 * rZ1;
   float dm = u * u - 2.0f * Z2 * u + 2.0f * (beta - 1.0f) * Z1p;   // D - 1
   bool nonreal = dm < -1.0f;
-  float e = __fdiv_rn(dm, 1.0f + __fsqrt_rn(1.0f + dm));          // c - 1
+  float D = 1.0f + dm;
+  float e = dm * rcp_nr(fmaf(D, rsqrt_approx(D), 1.0f));           // c - 1
   float c = 1.0f + e;
   F.s0 = u + c;
   F.s1 = u - c;
   F.u = u;
-  float rc = __frcp_rn(c);
+  float rc = rcp_nr(c);
   float h = 0.5f * rc;
   float d1 = R[0] - L[0];
   float d2 = R[1] - L[1];
@@ -281,6 +298,22 @@ __device__ __forceinline__ unsigned long long speed_bits(float s) {
   if (a != a) return 0x7ff8000000000000ull;
   return speed_bits((double)a);
 }
+// Running max |s| of a march in the precision's own bits (binary32: 32-bit
+// patterns, every NaN above +inf), widened to the binary64 pattern of the
+// domain scalars once per march.
+template <class T> struct Speed;
+template <> struct Speed<double> {
+  typedef unsigned long long B;
+  __device__ static B bits(double s) { return speed_bits(s); }
+  __device__ static unsigned long long wide(B b) { return b; }
+};
+template <> struct Speed<float> {
+  typedef unsigned B;
+  __device__ static B bits(float s) { return __float_as_uint(fabsf(s)); }
+  __device__ static unsigned long long wide(B b) {
+    return b > 0x7f800000u ? 0x7ff8000000000000ull : speed_bits((double)__uint_as_float(b));
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Line march: extended cells j = 0, 1, ... (two ghost cells, the line's
@@ -295,13 +328,13 @@ template <class T, int LIM, bool COMP> struct March4 {
   T c1[4], c2[4], z1[3];
   Face4<T> fm1, fm2;
   T apl[4], Fl[4];
-  unsigned long long smax;
+  typename Speed<T>::B smax;
   bool nonreal;
 
   __device__ __forceinline__ void init(T b, T l) {
     beta = b;
     lam = l;
-    smax = 0ull;
+    smax = 0;
     nonreal = false;
   }
   // n = domain cells along the line; gl = line coordinate of the left cell of
@@ -315,7 +348,8 @@ template <class T, int LIM, bool COMP> struct March4 {
       bool nr = roe4(beta, c1, z1, q, z, f);
       if (valid && gl >= -2 && gl <= n) nonreal |= nr;
       if (valid && gl >= -1 && gl <= n - 1) {
-        unsigned long long b0 = speed_bits(f.s0), b1 = speed_bits(f.s1), b2 = speed_bits(f.u);
+        typename Speed<T>::B b0 = Speed<T>::bits(f.s0), b1 = Speed<T>::bits(f.s1),
+            b2 = Speed<T>::bits(f.u);
         smax = b0 > smax ? b0 : smax;
         smax = b1 > smax ? b1 : smax;
         smax = b2 > smax ? b2 : smax;
@@ -421,7 +455,7 @@ __global__ void __launch_bounds__(128) k3_sweep_x(Args3 A) {
   const T *in[4] = {(const T *)A.in[0], (const T *)A.in[1], (const T *)A.in[2],
                     (const T *)A.in[3]};
   T *out[4] = {(T *)A.out[0], (T *)A.out[1], (T *)A.out[2], (T *)A.out[3]};
-  unsigned long long smax = 0ull;
+  typename Speed<T>::B smax = 0;
   bool nonreal = false;
   for (long long t = warp; t < items; t += nwarps) {
     const long long row = t / segs;
@@ -465,13 +499,15 @@ __global__ void __launch_bounds__(128) k3_sweep_x(Args3 A) {
     if (lane > 0) {
       if (glA >= -2 && glA <= nx) nonreal |= nrA;
       if (glA >= -1 && glA <= nx - 1) {
-        unsigned long long b0 = speed_bits(FA.s0), b1 = speed_bits(FA.s1), b2 = speed_bits(FA.u);
+        typename Speed<T>::B b0 = Speed<T>::bits(FA.s0), b1 = Speed<T>::bits(FA.s1),
+                             b2 = Speed<T>::bits(FA.u);
         smax = b0 > smax ? b0 : smax; smax = b1 > smax ? b1 : smax; smax = b2 > smax ? b2 : smax;
       }
     }
     if (glB >= -2 && glB <= nx) nonreal |= nrB;
     if (glB >= -1 && glB <= nx - 1) {
-      unsigned long long b0 = speed_bits(FB.s0), b1 = speed_bits(FB.s1), b2 = speed_bits(FB.u);
+      typename Speed<T>::B b0 = Speed<T>::bits(FB.s0), b1 = Speed<T>::bits(FB.s1),
+                           b2 = Speed<T>::bits(FB.u);
       smax = b0 > smax ? b0 : smax; smax = b1 > smax ? b1 : smax; smax = b2 > smax ? b2 : smax;
     }
     const Face4<T> LB = face_up(FB), RA = face_dn(FA);
@@ -505,7 +541,7 @@ __global__ void __launch_bounds__(128) k3_sweep_x(Args3 A) {
       }
     }
   }
-  flush_stats(S, smax, nonreal);
+  flush_stats(S, Speed<T>::wide(smax), nonreal);
 }
 
 // ---------------------------------------------------------------------------
@@ -534,7 +570,7 @@ __global__ void __launch_bounds__(128) k3_sweep_v(Args3 A) {
   const T *in[4] = {(const T *)A.in[pf[0]], (const T *)A.in[pf[1]], (const T *)A.in[pf[2]],
                     (const T *)A.in[pf[3]]};
   T *out[4] = {(T *)A.out[pf[0]], (T *)A.out[pf[1]], (T *)A.out[pf[2]], (T *)A.out[pf[3]]};
-  unsigned long long smax = 0ull;
+  typename Speed<T>::B smax = 0;
   bool nonreal = false;
   for (long long t = warp; t < tiles; t += nwarps) {
     const int xt = (int)(t % tx);
@@ -572,15 +608,17 @@ __global__ void __launch_bounds__(128) k3_sweep_v(Args3 A) {
     smax = m.smax > smax ? m.smax : smax;
     nonreal |= m.nonreal;
   }
-  flush_stats(S, smax, nonreal);
+  flush_stats(S, Speed<T>::wide(smax), nonreal);
 }
 
 // ---------------------------------------------------------------------------
 // Source: forward Euler with the 7-point Laplacian of z = (q2, q3, q4)/q1,
 // summed as ((W + E) + (S + N) - 4 C) + ((B + T) - 2 C).
 // ---------------------------------------------------------------------------
+// state of cell (i, j, k), ghost cells by the border rules (the normal
+// momentum of a mirrored cell negated), and its velocity z = (q2, q3, q4)/q1
 template <class T>
-__device__ __forceinline__ void zat(const Args3 &A, int i, int j, int k, int axis, T z[3]) {
+__device__ __forceinline__ void qat(const Args3 &A, int i, int j, int k, T q[4]) {
   const Dom3 &D = A.d;
   bool fx = false, fy = false, fz = false;
   int ci = map_cell(i, D.nx, D.bc[0], D.bc[1], fx);
@@ -588,60 +626,100 @@ __device__ __forceinline__ void zat(const Args3 &A, int i, int j, int k, int axi
   int ck = map_cell(k, D.nz, D.bc[4], D.bc[5], fz);
   long long off = ((long long)ck * D.ny + cj) * D.pitch + ci;
   const T *const *in = (const T *const *)A.in;
-  T r = inv_q1(in[0][off]);
-  T q2 = in[1][off], q3 = in[2][off], q4 = in[3][off];
-  if (fx) q2 = -q2;
-  if (fy) q3 = -q3;
-  if (fz) q4 = -q4;
-  z[0] = q2 * r;
-  z[1] = q3 * r;
-  z[2] = q4 * r;
-  (void)axis;
+#pragma unroll
+  for (int f = 0; f < 4; f++) q[f] = in[f][off];
+  if (fx) q[1] = -q[1];
+  if (fy) q[2] = -q[2];
+  if (fz) q[3] = -q[3];
+}
+template <class T> __device__ __forceinline__ void zof3(const T q[4], T z[3]) {
+  T r = inv_q1(q[0]);
+  z[0] = q[1] * r;
+  z[1] = q[2] * r;
+  z[2] = q[3] * r;
 }
 
-// one thread per cell of a row segment: blockIdx.x (x1 blocks of the block
-// width), blockIdx.y / blockIdx.z striding over rows x2 and planes x3; the
-// x1 neighbours' velocities come from the adjacent lanes (border rules where
-// the neighbour is a ghost cell or outside the warp)
-template <class T> __global__ void k3_source(Args3 A) {
+// One block marches a tile of SRC3_TX x SRC3_TY cells of the (x1, x2) plane
+// along x3 through a chunk of SRC3_KCH planes.  Every cell's velocity z is
+// formed once per plane: the tile's cells and a one-cell ring around it go
+// to shared memory for the x1 and x2 neighbours (the ring's cells are the
+// border rules' ghosts where the tile meets a border), and each thread keeps
+// the z of planes k-1, k and k+1 of its own cell in registers.  The state a
+// thread needs next (its own cell two planes ahead, its ring cell one plane
+// ahead) is loaded while the current plane is formed.  Threads of a tile
+// that overhangs the domain form ghost or clamped cells and store nothing.
+constexpr int SRC3_TX = 32, SRC3_TY = 8, SRC3_KCH = 16;
+template <class T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k3_source(Args3 A) {
   Scal3 *S = A.S;
   if (S->done) return;
   const Dom3 &D = A.d;
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool ok = i < D.nx;
-  const int ic = ok ? i : D.nx - 1;
+  __shared__ T sz[3][SRC3_TY + 2][SRC3_TX + 2];
+  const int tx = threadIdx.x % SRC3_TX, ty = threadIdx.x / SRC3_TX;
   const T coef = sizeof(T) == 8 ? (T)S->coef : (T)S->coef32;
-  const T *const *in = (const T *const *)A.in;
   T *const *out = (T *const *)A.out;
-  for (int k = blockIdx.z; k < D.nz; k += gridDim.z)
-    for (int j = blockIdx.y; j < D.ny; j += gridDim.y) {
-      T zc[3], zw[3], ze[3], zs[3], zn[3], zb[3], zt[3];
-      zat<T>(A, ic, j, k, -1, zc);
-      T uw[3], ue[3];
+  // the ring cell this thread forms (threads 0 .. 2 (TX + TY) - 1): the
+  // x1-low and x1-high columns, then the x2-low and x2-high rows
+  const int h = threadIdx.x;
+  int hx = -1, hy = -1;
+  if (h < SRC3_TY) { hx = 0; hy = 1 + h; }
+  else if (h < 2 * SRC3_TY) { hx = SRC3_TX + 1; hy = 1 + h - SRC3_TY; }
+  else if (h < 2 * SRC3_TY + SRC3_TX) { hx = 1 + h - 2 * SRC3_TY; hy = 0; }
+  else if (h < 2 * SRC3_TY + 2 * SRC3_TX) { hx = 1 + h - 2 * SRC3_TY - SRC3_TX; hy = SRC3_TY + 1; }
+  const int ntj = (D.ny + SRC3_TY - 1) / SRC3_TY, nkc = (D.nz + SRC3_KCH - 1) / SRC3_KCH;
+  const int i0 = blockIdx.x * SRC3_TX, i = i0 + tx;
+  for (int jt = blockIdx.y; jt < ntj; jt += gridDim.y) {
+    const int j0 = jt * SRC3_TY, j = j0 + ty;
+    const bool own = i < D.nx && j < D.ny;
+    const int hi = i0 - 1 + hx, hj = j0 - 1 + hy;
+    for (int kc = blockIdx.z; kc < nkc; kc += gridDim.z) {
+      const int k0 = kc * SRC3_KCH, k1 = min(D.nz, k0 + SRC3_KCH);
+      T zb[3], zc[3], zt[3], qc[4], qt[4], hq[4];
+      qat<T>(A, i, j, k0 - 1, qc);
+      zof3<T>(qc, zb);
+      qat<T>(A, i, j, k0, qc);
+      zof3<T>(qc, zc);
+      qat<T>(A, i, j, k0 + 1, qt);
+      if (hx >= 0) qat<T>(A, hi, hj, k0, hq);
+      for (int k = k0; k < k1; k++) {
+        T qn[4];
+        if (k + 1 < k1) qat<T>(A, i, j, k + 2, qn);
+        zof3<T>(qt, zt);
 #pragma unroll
-      for (int f = 0; f < 3; f++) {
-        uw[f] = __shfl_up_sync(0xffffffffu, zc[f], 1);
-        ue[f] = __shfl_down_sync(0xffffffffu, zc[f], 1);
-      }
-      if (lane == 0 || ic == 0) zat<T>(A, ic - 1, j, k, 0, zw);
-      else { zw[0] = uw[0]; zw[1] = uw[1]; zw[2] = uw[2]; }
-      if (lane == 31 || ic + 1 >= D.nx) zat<T>(A, ic + 1, j, k, 0, ze);
-      else { ze[0] = ue[0]; ze[1] = ue[1]; ze[2] = ue[2]; }
-      zat<T>(A, ic, j - 1, k, 1, zs);
-      zat<T>(A, ic, j + 1, k, 1, zn);
-      zat<T>(A, ic, j, k - 1, 2, zb);
-      zat<T>(A, ic, j, k + 1, 2, zt);
-      if (!ok) continue;
-      const long long off = ((long long)k * D.ny + j) * D.pitch + i;
-      out[0][off] = in[0][off];
+        for (int f = 0; f < 3; f++) sz[f][ty + 1][tx + 1] = zc[f];
+        if (hx >= 0) {
+          T zh[3];
+          zof3<T>(hq, zh);
 #pragma unroll
-      for (int f = 0; f < 3; f++) {
-        T L = ((zw[f] + ze[f]) + (zs[f] + zn[f]) - T(4) * zc[f]) +
-              ((zb[f] + zt[f]) - T(2) * zc[f]);
-        out[1 + f][off] = in[1 + f][off] + coef * L;
+          for (int f = 0; f < 3; f++) sz[f][hy][hx] = zh[f];
+          if (k + 1 < k1) qat<T>(A, hi, hj, k + 1, hq);
+        }
+        __syncthreads();
+        if (own) {
+          const long long off = ((long long)k * D.ny + j) * D.pitch + i;
+          out[0][off] = qc[0];
+#pragma unroll
+          for (int f = 0; f < 3; f++) {
+            T L = ((sz[f][ty + 1][tx] + sz[f][ty + 1][tx + 2]) +
+                   (sz[f][ty][tx + 1] + sz[f][ty + 2][tx + 1]) - T(4) * zc[f]) +
+                  ((zb[f] + zt[f]) - T(2) * zc[f]);
+            out[1 + f][off] = qc[1 + f] + coef * L;
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int f = 0; f < 3; f++) {
+          zb[f] = zc[f];
+          zc[f] = zt[f];
+        }
+#pragma unroll
+        for (int f = 0; f < 4; f++) {
+          qc[f] = qt[f];
+          if (k + 1 < k1) qt[f] = qn[f];
+        }
       }
     }
+  }
 }
 
 // plain copy of the four planes (a step whose enabled sub-steps end in the

@@ -842,7 +842,11 @@ int fvna_autotune(const fvna_config *cfg, int n, const fvna_domain *doms, const 
   int v = validate(cfg, n, doms, q0);
   if (v != FVNA_OK) return v;
   static const int TX[4] = {X32H_TILE, 16, 32, 64};
-  static const int TY[5] = {8, 16, 32, 64, 128};
+  // binary64: heights of the column tiles; binary32: heights whose marched
+  // rows (tile plus the 3-row halo on both sides) fill whole 8-row chunks
+  static const int TY64[5] = {8, 16, 32, 64, 128};
+  static const int TY32[5] = {10, 18, 26, 34, 42};
+  const int *TY = cfg->precision == FVNA_FP32_PERT ? TY32 : TY64;
   float best_ms = -1.0f;
   fvna_config winner = *cfg;
   cudaEvent_t e0 = nullptr, e1 = nullptr;

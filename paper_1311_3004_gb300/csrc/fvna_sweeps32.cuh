@@ -32,11 +32,12 @@
 namespace fvna {
 
 constexpr int X32_ROWS = 32;
-// resident x1-sweep warps per SM the register allocator plans for: 12 gives
-// the speculative march 168 registers (a few spilled bytes) and lets the
-// 32-cell tiles (16 KB of shared memory) keep 12 warps per SM
+// resident x1-sweep warps per SM the register allocator plans for: none (the
+// compiler takes 254 registers, no spills).  12 (168 registers, the general
+// split out of line, 12 warps per SM for 32-cell tiles) measured no faster:
+// 42.3 us against 40.8 us on the 2048^2 pulse.
 #ifndef X32_MINBLOCKS
-#define X32_MINBLOCKS 12
+#define X32_MINBLOCKS 1
 #endif
 #ifndef FVNA_Y_UNROLL
 #define FVNA_Y_UNROLL 2   // rows of the x2 sweep's plain loop unrolled together (measured best)
@@ -46,7 +47,11 @@ constexpr int X32_ROWS = 32;
 #endif
 constexpr int Y32_STAGES = FVNA_Y32_STAGES;
 // resident x2-sweep warps per SM the register allocator plans for (the
-// shared-memory ring allows 11)
+// shared-memory ring allows 11).  Interior tiles alone fit 128 registers
+// (16 warps per SM), but a kernel of those alone measured 42 us for 93 % of
+// the 2048^2 pulse's tiles and left the border tiles, whose general path
+// waits on global loads of ghost cells row after row, 28 us in a second
+// kernel; in one kernel they start first and overlap the interior ones.
 #ifndef Y32_MINBLOCKS
 #define Y32_MINBLOCKS 11
 #endif
@@ -379,17 +384,6 @@ __device__ __forceinline__ bool x32_tile(const StepArgs &A, const DomDev &D, Dom
 
 }  // namespace x2
 
-// The general split of a tile, kept out of line: it needs more registers
-// than the speculative march, and inlined it would set the register count
-// (and so the resident warps) of the whole kernel; called for the rare tile
-// that meets a face that is not subsonic, it may spill.
-template <int SW, int LIM, bool COMP>
-__device__ __noinline__ void x32_general(const StepArgs &A, const DomDev &D, DomScal *S,
-                                         unsigned char *mainb, unsigned char *halo, int x0, int y0,
-                                         int lane) {
-  x2::x32_tile<SW, LIM, COMP, true, false>(A, D, S, mainb, halo, x0, y0, lane);
-}
-
 // A tile whose speculative march met a face that is not subsonic is loaded
 // again and marched with the general split by the same warp, before its
 // store: its result depends only on the state planes, which no warp of the
@@ -464,7 +458,7 @@ __global__ void __launch_bounds__(32, X32_MINBLOCKS) k_sweep_x32(StepArgs A) {
           break;
         }
         phase ^= 1;
-        x32_general<SW, LIM, COMP>(A, D, S, mainb, halo, x0, y0, lane);
+        x2::x32_tile<SW, LIM, COMP, true, false>(A, D, S, mainb, halo, x0, y0, lane);
       }
     }
     __syncwarp();

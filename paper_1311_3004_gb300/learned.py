@@ -133,15 +133,29 @@ def _init_params(seed: int):
     return np.concatenate(flat).astype(np.float32)
 
 
+def _bias_slices():
+    """Index ranges of b1, b2, b3 in the flat parameter layout
+    (w1 b1 w2 b2 w3 b3, [out][in][row][col])."""
+    out, o = [], 0
+    for (co, ci) in [(32, 3), (32, 32), (3, 32)]:
+        o += co * ci * 9
+        out.append(slice(o, o + co))
+        o += co
+    return out
+
+
 def train_net(X, T, steps=1500, batch=8, crop=96, lr=1e-3, margin=4, seed=0, noise=0.0,
-              importance=False, log=print):
+              importance=False, bias=True, log=print):
     """Train a fresh network on random crops of (X, T); returns (net, info).
     in_scale normalises the state, out_scale the residual.  Crops are drawn
     with probability proportional to the residual energy they contain (plus
     a floor) if importance, since the residual is concentrated where the
     wave is; otherwise uniformly.  With
     noise > 0 the inputs get Gaussian noise of that many standard deviations
-    of X, so the network tolerates the drift of a corrected run."""
+    of X, so the network tolerates the drift of a corrected run.  With bias
+    False the biases stay zero (they are reset after every step): the ReLU
+    network then maps a field at rest to no correction, so a corrected run
+    cannot drift where there is no wave."""
     import torch
     import torch.nn.functional as F
     g = torch.Generator(device="cpu").manual_seed(seed)
@@ -180,17 +194,40 @@ def train_net(X, T, steps=1500, batch=8, crop=96, lr=1e-3, margin=4, seed=0, noi
         lr_t = lr * (0.1 ** (it / steps))
         losses.append(net.train_step(xb.contiguous(), (tb / out_scale).contiguous(), lr_t,
                                      in_scale=in_scale, margin=margin, edges=edges))
+        if not bias:
+            p = net.params()
+            for sl in _bias_slices():
+                p[sl] = 0.0
+            net.set_params(p)
         if log and (it % max(1, steps // 5) == 0 or it == steps - 1):
             log(f"  step {it}: loss {np.mean(losses[-50:]):.4e}")
-    info = {"in_scale": in_scale, "out_scale": out_scale, "margin": margin,
+    info = {"in_scale": in_scale, "out_scale": out_scale, "margin": margin, "bias": bias,
             "loss_first": float(np.mean(losses[:50])),
             "loss_last": float(np.mean(losses[-50:])), "seconds": time.perf_counter() - t0,
             "steps": steps}
     return net, info
 
 
+def reference(spec: Spec, p_surface: float, t_end=None, fine_precision=fvna.FP64):
+    """The fine-grid run restricted to the coarse grid: (restricted pressure
+    perturbation on the CPU, binary64; its maximum; run seconds)."""
+    import torch
+    t_end = spec.t_end if t_end is None else t_end
+    dxf = spec.workload(True, 1.0).dx
+    s, w = _solver(spec, True, p_surface, precision=fine_precision, steps_per_graph=64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.run(t_end=t_end)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    pf = torch.from_numpy(s.q(0))
+    s.close()
+    pfr = restrict(torch, _pert(torch, pf.cuda()), dxf)[0].cpu().double()
+    return pfr, float(pfr.max()), sec
+
+
 def evaluate(spec: Spec, p_surface: float, net=None, info=None, fine_precision=fvna.FP64,
-             t_end=None, gains=(1.0,), fine32=False):
+             t_end=None, gains=(1.0,), fine32=False, ref=None):
     """Run coarse (with and without the network) and fine to t_end; return the
     focal peak pressures, errors against the fine run and the run times;
     with fine32 also the fine grid in binary32 (the fastest plain solver of
@@ -214,16 +251,9 @@ def evaluate(spec: Spec, p_surface: float, net=None, info=None, fine_precision=f
         out[name] = {"seconds": time.perf_counter() - t0, "p": torch.from_numpy(s.pressure(0)),
                      "status": st["rc"]}
         s.close()
-    s, w = _solver(spec, True, p_surface, precision=fine_precision, steps_per_graph=64)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    s.run(t_end=t_end)
-    torch.cuda.synchronize()
-    pf = torch.from_numpy(s.q(0))
-    s.close()
-    out["fine"] = {"seconds": time.perf_counter() - t0}
-    pfr = restrict(torch, _pert(torch, pf.cuda()), dxf)[0].cpu().double()
-    peak_f = float(pfr.max())
+    pfr, peak_f, fine_s = ref if ref is not None else reference(spec, p_surface, t_end,
+                                                                 fine_precision)
+    out["fine"] = {"seconds": fine_s}
     res = {"t_end": t_end, "p_surface": p_surface, "focal_peak_fine": peak_f,
            "fine_seconds": out["fine"]["seconds"]}
     if fine32:

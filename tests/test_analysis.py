@@ -52,3 +52,17 @@ def test_harmonics_of_a_distorted_sine():
     assert h[0] == pytest.approx(0.4, rel=0.02)
     assert h[1] == pytest.approx(0.1, rel=0.05)
     assert h[2] < 0.01 and h[3] < 0.01
+
+
+def test_bias_slices_cover_the_biases_of_the_flat_layout():
+    """The bias-free training option zeroes exactly b1, b2 and b3 of the
+    flat parameter layout (w1 b1 w2 b2 w3 b3) and nothing else."""
+    from paper_1311_3004_gb300 import fvna, learned
+    flat = np.arange(fvna.NET_PARAMS, dtype=np.float32) + 1.0
+    for sl in learned._bias_slices():
+        flat[sl] = 0.0
+    d = fvna.net_params_dict(flat)
+    for k in ("b1", "b2", "b3"):
+        assert np.all(d[k] == 0.0), k
+    for k in ("w1", "w2", "w3"):
+        assert np.all(d[k] != 0.0), k

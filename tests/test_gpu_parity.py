@@ -370,8 +370,9 @@ def test_fp32_faces_that_are_not_subsonic(flow, tile_x):
     binary32 sweep along the flow marches its tiles with the subsonic split
     first, finds faces where it does not hold and marches those tiles again
     with the general split; the result matches the oracle, whose split is
-    the general one everywhere."""
-    n = 80
+    the general one everywhere.  136 cells a side: the x2 sweep has
+    interior tiles (its first kernel lists them) as well as border tiles."""
+    n = 136
     q = wl.random_smooth(n, n, 1e-3, seed=61)
     q[1] += flow[0] * q[0]
     q[2] += flow[1] * q[0]
@@ -486,7 +487,7 @@ def test_batched_domains_fp32_and_autotune():
     cfg = gpu_config(cases[0], fvna.FP32_PERT)
     doms = [gpu_domain(c) for c in cases]
     best, ms = fvna.autotune(cfg, doms, [c.q0 for c in cases], trial_steps=4)
-    assert best.tile_x in (60, 16, 32, 64) and best.tile_y in (8, 16, 32, 64, 128) and ms > 0
+    assert best.tile_x in (60, 16, 32, 64) and best.tile_y in (10, 18, 26, 34, 42) and ms > 0
     s = fvna.Solver(best, doms, [c.q0 for c in cases])
     s.run(max_steps=60)
     for k, c in enumerate(cases):
