@@ -295,9 +295,10 @@ def record_traffic(csv_path: str, out_path: str, n: int = N_SIDE, n3: int = 256)
         key = (int(r[ci["ID"]]), r[ci["Kernel Name"]])
         per_launch[key] = per_launch.get(key, 0.0) + v
     out = {"_note": ("dram__bytes_read.sum + dram__bytes_write.sum per launch, averaged over "
-                     "the captured launches, from " + os.path.basename(csv_path) + "; valid "
-                     "while the kernel sources hash to source_digest (written by bench.py "
+                     "the captured launches of the ncu CSV named in `capture`; valid while "
+                     "the kernel sources hash to source_digest (written by bench.py "
                      "--record-traffic, never by hand)")}
+    cap = os.path.basename(csv_path)
     digest = source_digest()
     try:
         old = json.load(open(out_path))
@@ -311,7 +312,7 @@ def record_traffic(csv_path: str, out_path: str, n: int = N_SIDE, n3: int = 256)
         if ids:
             out[f"{key}_{n3}"] = {"dram_bytes_per_launch":
                                   int(round(sum(per_launch[k] for k in ids) / len(ids))),
-                                  "launches": len(ids),
+                                  "launches": len(ids), "capture": cap,
                                   "source_digest": source_digest(_SWEEP3_SOURCES)}
     for pat, key in _TRAFFIC_KEYS:
         # launches in capture order; the x2 sweep's second kernel follows its first
@@ -324,7 +325,7 @@ def record_traffic(csv_path: str, out_path: str, n: int = N_SIDE, n3: int = 256)
         if launches == 0:
             continue
         out[f"{key}_{n}x{n}"] = {"dram_bytes_per_launch": int(round(tot / launches)),
-                                 "launches": launches, "source_digest": digest}
+                                 "launches": launches, "capture": cap, "source_digest": digest}
     with open(out_path, "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")

@@ -11,6 +11,7 @@ crops).
 
     X, T = generate(spec, amplitudes)        # solver-made training data
     net, info = train_net(X, T, steps)       # on the GPU, our kernels
+    X2, T2 = generate_rollout(spec, amplitudes, net, info)   # on its own trajectory
     result = evaluate(spec, amp, net, info)  # coarse+net vs coarse vs fine
 """
 from __future__ import annotations
@@ -119,6 +120,54 @@ def generate(spec: Spec, amplitudes, log=print):
         sf.close()
         if log:
             log(f"  amplitude {a / 1e6:.2f} MPa: {k} samples, {time.perf_counter() - t0:.1f} s")
+    return torch.stack(xs), torch.stack(ts)
+
+
+def generate_rollout(spec: Spec, amplitudes, net, info, gain=0.5, log=print):
+    """Training samples on the corrected coarse run's own trajectory (data
+    aggregation): at each sample time t_a the corrected coarse state Y is
+    advanced `every` plain coarse steps to X', and the target is the
+    restricted fine state at t_a + every coarse steps minus X'.  The network
+    so learns to steer the states its own corrections lead to back towards
+    the fine solution.  A run whose correction makes it fail stops adding
+    samples."""
+    import torch
+    xs, ts = [], []
+    dxf = spec.workload(True, 1.0).dx
+    k_ = spec.every
+    for a in amplitudes:
+        t0 = time.perf_counter()
+        sf, wf = _solver(spec, True, a, steps_per_graph=2 * spec.sample_every)
+        sc, wc = _solver(spec, False, a, steps_per_graph=spec.sample_every)
+        sc.set_correction(net, info["in_scale"], gain * info["out_scale"], spec.every,
+                          edge_band=spec.band)
+        qf = torch.empty((3, wf.ny, wf.nx), dtype=torch.float64, device="cuda")
+        qc = torch.empty((3, wc.ny, wc.nx), dtype=torch.float64, device="cuda")
+        t_now, k = 0.0, 0
+        while t_now < spec.t_train:
+            sf.run(max_steps=2 * max(spec.sample_every - k_, 0))
+            st = sc.run(max_steps=max(spec.sample_every - k_, 0), check=False)
+            if st["rc"] != 0:
+                break
+            ta = sc.stats(0)["t"]
+            Y = sc.q(0, out=qc).clone()
+            sf.run(max_steps=2 * k_)
+            B = restrict(torch, _pert(torch, sf.q(0, out=qf)), dxf)
+            sx, _ = _solver(spec, False, a, q0=Y, t0=ta)
+            sx.run(max_steps=k_)
+            X = _pert(torch, sx.q(0, out=torch.empty_like(Y)))
+            sx.close()
+            st = sc.run(max_steps=k_, check=False)
+            t_now = sf.stats(0)["t"]
+            xs.append(X)
+            ts.append(B - X)
+            k += 1
+            if st["rc"] != 0:
+                break
+        sf.close()
+        sc.close()
+        if log:
+            log(f"  rollout at {a / 1e6:.2f} MPa: {k} samples, {time.perf_counter() - t0:.1f} s")
     return torch.stack(xs), torch.stack(ts)
 
 
