@@ -379,6 +379,39 @@ template <class T, int LIM, bool COMP> struct March4 {
     z1[0] = z[0]; z1[1] = z[1]; z1[2] = z[2];
     return done;
   }
+  // push of a cell j >= 4 (no start-up cases, so that consecutive cells can
+  // be interleaved): the same operations as push, returning the update of
+  // cell j - 2
+  __device__ __forceinline__ void step(const T q[4], T out[4], int gl, int n, bool valid) {
+    T r = inv_q1(q[0]);
+    T z[3] = {q[1] * r, q[2] * r, q[3] * r};
+    Face4<T> f;
+    bool nr = roe4(beta, c1, z1, q, z, f);
+    if (valid && gl >= -2 && gl <= n) nonreal |= nr;
+    if (valid && gl >= -1 && gl <= n - 1) {
+      typename Speed<T>::B b0 = Speed<T>::bits(f.s0), b1 = Speed<T>::bits(f.s1),
+          b2 = Speed<T>::bits(f.u);
+      smax = b0 > smax ? b0 : smax;
+      smax = b1 > smax ? b1 : smax;
+      smax = b2 > smax ? b2 : smax;
+    }
+    T am[4], ap[4], F[4];
+    flux4<LIM, T>(fm1, fm2, f, lam, am, ap, F);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      out[k] = update<COMP>(c2[k], am[k], apl[k], F[k], Fl[k], lam);
+      apl[k] = ap[k];
+      Fl[k] = F[k];
+    }
+    fm2 = fm1;
+    fm1 = f;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      c2[k] = c1[k];
+      c1[k] = q[k];
+    }
+    z1[0] = z[0]; z1[1] = z[1]; z1[2] = z[2];
+  }
 };
 
 // warp-wide statistics of a march into the scalars
@@ -585,21 +618,33 @@ __global__ void __launch_bounds__(128) k3_sweep_v(Args3 A) {
     const int len = min(TY, n - g0) + 4;
     March4<T, LIM, COMP> m;
     m.init((T)A.beta, lam);
+    // a tile whose marched cells (two halo cells at each end) all lie inside
+    // the line reads them without the border rules
+    const bool inner = g0 >= 2 && g0 + len - 3 <= n - 1;
     auto load = [&](int j, T q[4]) {
-      bool flip;
-      int c = map_cell(g0 - 2 + j, n, bclo, bchi, flip);
-      long long off = base + (long long)c * stride;
+      bool flip = false;
+      const int c = inner ? g0 - 2 + j : map_cell(g0 - 2 + j, n, bclo, bchi, flip);
+      const long long off = base + (long long)c * stride;
 #pragma unroll
       for (int k = 0; k < 4; k++) q[k] = in[k][off];
       if (flip) q[1] = -q[1];
     };
     T nxt[4];
     load(0, nxt);
-    for (int j = 0; j < len; j++) {
+    // start-up: cells 0..3 (no update yet); len >= 5
+    for (int j = 0; j < 4; j++) {
+      T q[4] = {nxt[0], nxt[1], nxt[2], nxt[3]};
+      load(j + 1, nxt);
+      T ov[4];
+      m.push(j, q, ov, g0 - 3 + j, n, valid);
+    }
+#pragma unroll 2
+    for (int j = 4; j < len; j++) {
       T q[4] = {nxt[0], nxt[1], nxt[2], nxt[3]};
       if (j + 1 < len) load(j + 1, nxt);
       T ov[4];
-      if (m.push(j, q, ov, g0 - 3 + j, n, valid) && valid) {
+      m.step(q, ov, g0 - 3 + j, n, valid);
+      if (valid) {
         long long off = base + (long long)(g0 + j - 4) * stride;
 #pragma unroll
         for (int k = 0; k < 4; k++) out[k][off] = ov[k];

@@ -486,8 +486,6 @@ struct YCol {
   bool plain;    // rows inside the domain read column col unchanged
   bool xdrv;     // driven ghost column (analytic values replace the swept ones)
   bool upd;      // updated and accounted column of this tile
-  int scol;      // plain ghost column: where its mapped column sits in the tile's
-                 // shared-memory rows (-1: outside the box, read from global memory)
 };
 
 __device__ __forceinline__ YCol ycol(const DomDev &D, int gx, int x0, int lane) {
@@ -509,28 +507,16 @@ __device__ __forceinline__ YCol ycol(const DomDev &D, int gx, int x0, int lane) 
     else if (bc == BC_HIFU && side == 0) { c.col = 0; c.xdrv = true; }
     else c.col = side == 0 ? 0 : nx - 1;
   }
-  // the box of a chunk row starts 4 columns left of the tile
-  const int sc = c.col - (x0 - 4);
-  c.scol = !c.inside && c.plain && c.col >= 0 && c.col < nx && sc >= 0 && sc < YBOX ? sc : -1;
   return c;
 }
 
-// value of (gx, gy) for a border tile: shared memory for inside cells and
-// for ghost columns that copy a column of the tile's box (extrapolation, or
-// a periodic partner within reach), the border rules for the rest (the same
-// values as the binary64 sweep).  rowp: the chunk row of gy in shared memory.
+// value of (gx, gy) for a border tile: shared memory for inside cells, the
+// border rules for the rest (the same reads as the binary64 sweep)
 __device__ __forceinline__ void ycell(const DomDev &D, const YCol &c, int gy,
-                                      const float *const q[3], const unsigned char *rowp,
-                                      float s0, float s1, float s2, float v[3]) {
+                                      const float *const q[3], float s0, float s1, float s2,
+                                      float v[3]) {
   if (c.inside && gy >= 0 && gy < D.ny) {
     v[0] = s0; v[1] = s1; v[2] = s2;
-    return;
-  }
-  if (c.scol >= 0 && gy >= 0 && gy < D.ny) {
-    const unsigned char *p = rowp + c.scol * 4;
-    v[0] = *(const float *)p;
-    v[1] = *(const float *)(p + YRB * YBOX * 4);
-    v[2] = *(const float *)(p + 2 * YRB * YBOX * 4);
     return;
   }
   if (c.plain && gy >= 0 && gy < D.ny && chk(c.col >= 0 && c.col < D.nx, 3, c.col)) {
@@ -711,15 +697,14 @@ __device__ __forceinline__ int y32_tile(const StepArgs &A, const DomDev &D, DomS
     const int rows = min(YRB, nrows - c * YRB);
     auto fetch = [&](int i, int j) {
       const int gy = y0 - HALO_Y + j;
-      const unsigned char *row = st + i * (YBOX * 4);
-      const unsigned char *rp = row + (2 + 2 * lane) * 4;
+      const unsigned char *rp = st + i * (YBOX * 4) + (2 + 2 * lane) * 4;
       float2 f0 = *(const float2 *)(rp);
       float2 f1 = *(const float2 *)(rp + YRB * YBOX * 4);
       float2 f2 = *(const float2 *)(rp + 2 * YRB * YBOX * 4);
       float v[3];
-      ycell(D, ca, gy, qi, row, f0.x, f1.x, f2.x, v);
+      ycell(D, ca, gy, qi, f0.x, f1.x, f2.x, v);
       f0.x = v[0]; f1.x = v[1]; f2.x = v[2];
-      ycell(D, cb, gy, qi, row, f0.y, f1.y, f2.y, v);
+      ycell(D, cb, gy, qi, f0.y, f1.y, f2.y, v);
       f0.y = v[0]; f1.y = v[1]; f2.y = v[2];
       // march order of the x2 sweep: (q1 - 1, q3, q2)
       Cell q;
