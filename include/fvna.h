@@ -97,8 +97,11 @@ typedef struct fvna_config {
   double nu_max;        /* a step with nu > nu_max ends the run with FVNA_ERR_CFL */
   double dt_fixed;      /* > 0: use this dt for every step instead of the CFL rule */
   int steps_per_graph;  /* steps captured per CUDA graph replay; 0 = default (32) */
-  int tile_x;           /* x1-sweep tile width (16, 32 or 64 cells per warp row); 0 = default */
-  int tile_y;           /* x2-sweep tile height (rows per warp); 0 = default */
+  int tile_x;           /* x1-sweep tile width (16, 32 or 64 cells per warp row; binary32 also
+                           60: the x1 sweep with the lanes along x1); 0 = default (picked
+                           from the domain sizes) */
+  int tile_y;           /* x2-sweep tile height (rows per warp); 0 = default (binary64 64,
+                           binary32 10: 16 marched rows, two whole 8-row chunks) */
   int compensated;      /* FVNA_FP32_PERT: 0 = the increments of eq. fv-hr summed and added
                            to the state in one fused multiply-add (one rounding of the sum;
                            the default), 1 = the state and the two increments summed with

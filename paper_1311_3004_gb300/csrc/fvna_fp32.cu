@@ -141,17 +141,37 @@ int occupancy_y_fp32(int lim, int comp) {
   return n;
 }
 
+// The binary32 sweeps launch as programmatic dependents of the kernel before
+// them in the stream (the kernels wait for it before their first global
+// access): a sweep's blocks are scheduled while the previous kernel's last
+// blocks finish, and in a captured graph the edges between the sweeps are
+// programmatic ones.
+static cudaError_t launch_dependent(StepKernel k, int blocks, int smem, cudaStream_t s,
+                                    const StepArgs &a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, a);
+}
+
 cudaError_t launch_sweep_x_fp32(int tile_x, const StepArgs &a, int blocks, cudaStream_t s) {
-  px(tile_x, a.limiter, a.compensated != 0)<<<blocks, 32, smem_x32(tile_x), s>>>(a);
-  return cudaGetLastError();
+  return launch_dependent(px(tile_x, a.limiter, a.compensated != 0), blocks, smem_x32(tile_x), s,
+                          a);
 }
 cudaError_t launch_sweep_y_fp32(const StepArgs &a, int blocks, cudaStream_t s) {
-  py<false>(a.limiter, a.compensated != 0)<<<blocks, 32, y32_smem_bytes(), s>>>(a);
-  return cudaGetLastError();
+  return launch_dependent(py<false>(a.limiter, a.compensated != 0), blocks, y32_smem_bytes(), s,
+                          a);
 }
 cudaError_t launch_sweep_y_redo32(const StepArgs &a, int blocks, cudaStream_t s) {
-  py<true>(a.limiter, a.compensated != 0)<<<blocks, 32, y32_smem_bytes(), s>>>(a);
-  return cudaGetLastError();
+  return launch_dependent(py<true>(a.limiter, a.compensated != 0), blocks, y32_smem_bytes(), s,
+                          a);
 }
 
 size_t ghost_ring_bytes(int nx, int ny) { return 3 * x2::ghost_ring_size(nx, ny) * sizeof(float); }

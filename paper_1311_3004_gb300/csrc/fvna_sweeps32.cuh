@@ -401,6 +401,7 @@ __global__ void __launch_bounds__(32, X32_MINBLOCKS) k_sweep_x32(StepArgs A) {
   const int lane = threadIdx.x;
   const Maps *maps = (const Maps *)A.tmaps;
   if (lane == 0) mbar_init(bar, 1);
+  griddep_wait();
   if (blockIdx.x == 0 && lane == 0) {
     A.counters[1] = 0u;         // the x2 sweep's tile counter
     A.redo[1] = 0;              // the x2 sweep's list, empty for this step
@@ -470,6 +471,7 @@ __global__ void __launch_bounds__(32, X32_MINBLOCKS) k_sweep_x32(StepArgs A) {
       bulk_commit();
     }
   }
+  griddep_launch();
   if (lane == 0) bulk_wait();
 }
 
@@ -805,6 +807,7 @@ __global__ void __launch_bounds__(32, Y32_MINBLOCKS) k_sweep_y32(StepArgs A) {
   uint64_t *bars = (uint64_t *)(ring + Y32_STAGES * Y32_STAGE_BYTES);
   const int lane = threadIdx.x;
   const Maps *maps = (const Maps *)A.tmaps;
+  griddep_wait();
   const int nredo = REDO ? A.redo[1] : 0;
   if (REDO && nredo == 0) {
     // nothing to redo: every statistic of the step is in (the first kernel
@@ -850,6 +853,7 @@ __global__ void __launch_bounds__(32, Y32_MINBLOCKS) k_sweep_y32(StepArgs A) {
     if (rc == 1) break;
     it = REDO ? cur + (int)gridDim.x : take_tile_collect(tn);
   }
+  griddep_launch();
   if (REDO) y32_finish_step(A, lane, true);
 }
 

@@ -89,6 +89,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
 // an error, waits once more with the default limit for the copy to land, and
 // stops using the buffer).
 constexpr int WAIT_LIMIT = 1 << 22;
+
+// Programmatic dependent launch of the binary32 sweeps: griddep_wait blocks
+// until the grid this one follows in the stream has completed and its
+// memory is visible (at once in a launch without the attribute, or when
+// that grid has already completed); griddep_launch lets the next grid start
+// launching once every block of this one has called it or exited.  Each
+// sweep kernel waits before its first global access and signals when its
+// block takes no more tiles.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity,
                                           int limit = WAIT_LIMIT) {
   for (int i = 0; i < limit; i++)

@@ -203,6 +203,7 @@ template <int LIM, bool COMP>
 __global__ void __launch_bounds__(32, XH_MINBLOCKS) k_sweep_x32h(StepArgs A) {
   using namespace x2;
   const int lane = threadIdx.x;
+  griddep_wait();
   if (blockIdx.x == 0 && lane == 0) {
     A.counters[1] = 0u;         // the x2 sweep's tile counter
     A.redo[1] = 0;              // the x2 sweep's list, empty for this step
@@ -249,6 +250,7 @@ __global__ void __launch_bounds__(32, XH_MINBLOCKS) k_sweep_x32h(StepArgs A) {
     }
     it = take_tile_collect(tn);
   }
+  griddep_launch();
   if (cur >= 0) flush_acc(tot, A.scal + cur, lane);
 }
 
