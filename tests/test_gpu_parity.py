@@ -498,3 +498,21 @@ def test_batched_domains_fp32_and_autotune():
     ts = [s.stats(k)["t"] for k in range(len(cases))]
     assert len(set(ts)) > 1      # every domain kept its own dt
     s.close()
+
+
+@pytest.mark.parametrize("nx,ny,bc", [(1, 1, (E, E, E, E)), (3, 5, (P, P, E, E)),
+                                      (257, 129, (R, E, P, P))])
+def test_tiny_and_odd_sizes(nx, ny, bc):
+    """The smallest domain, a 3x5 periodic-extrapolated one and a 257x129
+    mixed one (one cell past a power of two each way): binary64 equal to the
+    oracle, binary32 within 1e-5 of it."""
+    q = wl.random_cells(nx, ny, 1e-3, seed=nx * 1000 + ny)
+    c = Case(nx, ny, q, bc=bc, delta=1e-3)
+    qo, so = run_oracle(c, 20)
+    assert so["status"] == 0
+    qg, sg = run_gpu(c, 20)
+    assert sg["rc"] == 0 and sg["steps"] == so["step"]
+    assert pert_rel_linf(qg, qo) <= TOL64
+    q32, s32 = run_gpu(c, 20, precision=fvna.FP32_PERT)
+    assert s32["rc"] == 0 and s32["steps"] == so["step"]
+    assert pert_rel_linf(q32, qo) <= TOL32
